@@ -1,0 +1,155 @@
+/*
+ * dfmm.h — C ABI of the GB300 directional fast multipole matvec.
+ *
+ * The library computes, for N points p_i in R^3 and densities f_j,
+ *
+ *     u_i = sum_{j : p_j != p_i} G(p_i, p_j) f_j,   G(x, y) = exp(2 pi i |x-y|) / |x-y|
+ *
+ * (Eq. 1 of Benson, Poulson, Tran, Engquist, Ying, "A parallel directional
+ * fast multipole method", arXiv:1311.4257; wavelength 1, |p_i| <= K/2).  The
+ * self term G(p_i, p_i) is infinite; every source whose point is bitwise equal
+ * to the target point is skipped.
+ *
+ * The method is the sequential directional FMM of Alg. 1 (Sec. 2.3): an
+ * octree that is uniform in the high-frequency regime (box width w >= 1) and
+ * adaptive below it (Sec. 2.2); directional low-rank representations
+ * (Eq. 2, Sec. 2.1) with M2M / M2L / L2L translations over the directional
+ * interaction lists for w >= 1 and kernel-independent FMM lists below; and a
+ * direct near-field sum.
+ *
+ * Conventions
+ *  - Every call returns a dfmm_status (0 on success).  On failure the message
+ *    of the calling thread's last error is available from dfmm_last_error().
+ *  - "device pointer" means memory of the current CUDA device, allocated by
+ *    the caller (cudaMalloc, torch, ...).  "host pointer" means ordinary host
+ *    memory.  The library never frees caller memory.
+ *  - Complex numbers are interleaved (re, im) pairs of the stated float type.
+ *  - A plan is immutable after dfmm_plan returns and is owned by the library
+ *    until dfmm_destroy.  Applies on one plan may be issued from several host
+ *    threads on different streams: each stream gets its own workspace.
+ */
+#ifndef DFMM_H
+#define DFMM_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dfmm_plan_s* dfmm_plan_t;   /* opaque, owned by the library */
+
+typedef enum {
+  DFMM_OK = 0,
+  DFMM_ERR_INVALID = -1,      /* bad argument (null pointer, N < 1, nrhs < 1, ...) */
+  DFMM_ERR_DOMAIN = -2,       /* a point lies outside the root box |x|_inf <= K/2 */
+  DFMM_ERR_OOM = -3,          /* device or host allocation failed */
+  DFMM_ERR_CUDA = -4,         /* a CUDA runtime / cuBLAS call failed */
+  DFMM_ERR_UNSUPPORTED = -5,  /* eps outside [1e-8, 1e-2], K outside (0, 4096] */
+  DFMM_ERR_TIMEOUT = -6,      /* a device-side bounded wait gave up */
+  DFMM_ERR_DEVICE = -7        /* a device-side check failed (status word set) */
+} dfmm_status;
+
+/* Plan-time options.  Zero-initialise and set what you need; zero fields take
+ * the defaults given in brackets. */
+typedef struct {
+  int32_t leaf_max;        /* [64] an LF box with more points is split (Sec. 2.2) */
+  int32_t sample_box;      /* [1024] box samples per skeleton */
+  int32_t sample_far;      /* [4096] far-region samples per skeleton */
+  int32_t sketch_rows;     /* [400] rows of the random sketch in the pivoted QR */
+  double eps_op_factor;    /* [0.1] skeleton tolerance = eps * factor */
+  int32_t m2l_mode;        /* [0] 0 = tensor cores (split TF32) when built for it, 1 = FP32 CUDA cores */
+  int32_t host_threads;    /* [0 = all cores] threads for the skeleton precompute */
+  const char* cache_dir;   /* [NULL = no disk cache] directory for skeleton files */
+} dfmm_options;
+
+/* Build a plan (Sec. 2.2 octree, lists, Eq. 2 representations and the
+ * translation operators).
+ *   points : device pointer, float64, row-major [N][3], caller order.  Read
+ *            during the call only; the plan keeps its own copies.
+ *   N      : number of points, >= 1.
+ *   K      : domain size in wavelengths; every point must satisfy
+ *            max_d |p_d| <= K/2 (else DFMM_ERR_DOMAIN).  0 < K <= 4096.
+ *   eps    : requested relative accuracy, 1e-8 <= eps <= 1e-2.
+ *   opts   : host pointer to options, or NULL for the defaults.
+ *   out    : host pointer receiving the plan handle.
+ * Runs on the current device and the legacy default stream; synchronises the
+ * device before returning. */
+int dfmm_plan(const double* points, int64_t N, double K, double eps,
+              const dfmm_options* opts, dfmm_plan_t* out);
+
+/* The matvec u = G f (Alg. 1 passes plus the near field).
+ *   f      : device pointer, complex64 [nrhs][N] in the caller's point order.
+ *   u      : device pointer, complex64 [nrhs][N]; overwritten, never
+ *            accumulated.  Must not alias f.
+ *   nrhs   : number of right-hand sides, 1 <= nrhs <= 64.
+ *   stream : CUDA stream; the call only enqueues work (no host sync).
+ * The workspace of (plan, stream) is allocated on the first call with that
+ * stream and nrhs at least as large; it is reused afterwards. */
+int dfmm_apply(dfmm_plan_t plan, const void* f, void* u, int nrhs, cudaStream_t stream);
+
+/* Same as dfmm_apply with host (pageable or pinned) f and u: copies f to the
+ * device, applies, copies u back, and synchronises the stream. */
+int dfmm_apply_host(dfmm_plan_t plan, const void* f_host, void* u_host, int nrhs,
+                    cudaStream_t stream);
+
+/* Read back the device status word of the last apply on `stream`
+ * (synchronises the stream).  Returns DFMM_OK, DFMM_ERR_TIMEOUT or
+ * DFMM_ERR_DEVICE. */
+int dfmm_sync_status(dfmm_plan_t plan, cudaStream_t stream);
+
+/* Free every resource of the plan (waits for the device first). */
+int dfmm_destroy(dfmm_plan_t plan);
+
+/* Sizes and counts of a plan, for reports and tests. */
+typedef struct {
+  int64_t N;
+  double K, W, eps, eps_op;
+  int32_t n_levels;            /* octree levels (root = 0) */
+  int32_t level_hf_top;        /* coarsest level with a non-empty HF list */
+  int32_t level_w1;            /* level of width 1 */
+  int64_t boxes[32];           /* non-empty boxes per level */
+  int64_t leaves[32];          /* leaves per level */
+  int64_t hf_pairs[32];        /* HF-M2L pairs per level */
+  int64_t hf_offsets[32];      /* distinct HF-M2L offsets (operators) per level */
+  int64_t slots_out[32];       /* active outgoing (box, direction) per level */
+  int64_t slots_in[32];        /* active incoming (box, direction) per level */
+  int32_t rank[32];            /* padded representation rank per level */
+  int64_t v_pairs, u_pairs, w_pairs, x_pairs;
+  int64_t p2p_interactions;    /* sum over U pairs of n_target * n_source */
+  int64_t plan_bytes;          /* device bytes held by the plan */
+  double plan_seconds;         /* wall time of dfmm_plan */
+  double m2l_flops;            /* algorithmic M2L flops per RHS: 8 r_t r_s per pair */
+  double other_translation_flops; /* M2M, L2L, LF-M2L, P2M/L2P GEMMs per RHS */
+} dfmm_stats;
+
+int dfmm_plan_stats(dfmm_plan_t plan, dfmm_stats* out);
+
+/* Device bytes of the per-stream workspace that an apply with nrhs needs. */
+int64_t dfmm_apply_workspace_bytes(dfmm_plan_t plan, int nrhs);
+
+/* Export of the plan's tree and lists for parity tests (host buffers).
+ * Call with a NULL buffer to get the required element count in *count.
+ *   what = 0: Morton permutation, int64 [N]
+ *          1: sorted Morton keys, uint64 [N]
+ *          2: boxes, int64 [n][5] = (level, key prefix, first, count, leaf)
+ *          3: HF-M2L pairs, int64 [n][5] = (level, target box, source box,
+ *             incoming direction, outgoing direction), box = index within level
+ *          4: active outgoing slots, int64 [n][3] = (level, box, direction)
+ *          5: active incoming slots, int64 [n][3]
+ *          6: V pairs, int64 [n][3] = (level, target, source)
+ *          7: U pairs, int64 [n][4] = (target level, target, source level, source)
+ *          8: W pairs, int64 [n][4] (target leaf level, leaf, source level, box)
+ *          9: X pairs, int64 [n][4] (target level, box, source level, leaf)
+ *         10: ranks of every representation type, int64 [n][3] = (level, cell or -1, rank)
+ */
+int dfmm_export(dfmm_plan_t plan, int what, void* buffer, int64_t* count);
+
+/* Thread-local message of the last failed call on this thread. */
+const char* dfmm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DFMM_H */
