@@ -58,7 +58,7 @@ typedef struct {
   int32_t sample_box;      /* [1024] box samples per skeleton */
   int32_t sample_far;      /* [4096] far-region samples per skeleton */
   int32_t sketch_rows;     /* [400] rows of the random sketch in the pivoted QR */
-  double eps_op_factor;    /* [0.1] skeleton tolerance = eps * factor */
+  double eps_op_factor;    /* [0.3] skeleton tolerance = eps * factor */
   int32_t m2l_mode;        /* [0] 0 = tensor cores (split TF32) when built for it, 1 = FP32 CUDA cores */
   int32_t host_threads;    /* [0 = all cores] threads for the skeleton precompute */
   const char* cache_dir;   /* [NULL = no disk cache] directory for skeleton files */
@@ -145,6 +145,21 @@ int64_t dfmm_apply_workspace_bytes(dfmm_plan_t plan, int nrhs);
  *         10: ranks of every representation type, int64 [n][3] = (level, cell or -1, rank)
  */
 int dfmm_export(dfmm_plan_t plan, int what, void* buffer, int64_t* count);
+
+/* Host-only (no device work): build one representation type of Eq. 2 the
+ * way dfmm_plan does, for inspection and tests.
+ *   w       : box width (a power of two); cell: face-cell index (w >= 1) or
+ *             -1 for the non-directional low-frequency type (w < 1).
+ *   w_top   : coarsest width whose representations are evaluated.
+ *   eps_op  : skeleton tolerance; sample_box, sample_far, sketch_rows as in
+ *             dfmm_options (0 = default).
+ *   r_out   : receives the rank r.
+ *   b2, a2  : host buffers of at least 6*cap doubles, or NULL; on return they
+ *             hold the 2r box check points (first r = equivalent points) and
+ *             the 2r far check points, [2r][3] row-major, box-centred frame.
+ *   cap     : capacity of b2/a2 in points; DFMM_ERR_INVALID if 2r > cap. */
+int dfmm_representation(double w, int cell, double w_top, double eps_op, int sample_box, int sample_far,
+                        int sketch_rows, int* r_out, double* b2, double* a2, int cap);
 
 /* Thread-local message of the last failed call on this thread. */
 const char* dfmm_last_error(void);

@@ -1,0 +1,7 @@
+"""GB300-native directional fast multipole matvec (arXiv:1311.4257).
+
+The compute path is the CUDA library libdfmm.so (C ABI in include/dfmm.h);
+this package holds its sources (csrc/), the build script and a thin ctypes
+binding (dfmm.py).
+"""
+from .dfmm import Plan, DfmmError, representation, lib  # noqa: F401

@@ -1,0 +1,71 @@
+"""Build libdfmm.so in-tree with nvcc for sm_103a (one nvcc per translation
+unit, in parallel, then one link)."""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+BUILD = os.path.join(HERE, "_build")
+LIB = os.path.join(HERE, "libdfmm.so")
+
+SOURCES = ["sort.cu", "tree.cu", "operators.cu", "apply.cu", "m2l_tc.cu", "skeleton.cpp", "dfmm.cpp"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def nvcc() -> str:
+    p = shutil.which("nvcc") or "/usr/local/cuda/bin/nvcc"
+    if not os.path.exists(p):
+        raise RuntimeError("nvcc not found")
+    return p
+
+
+def _flags(src: str) -> list[str]:
+    f = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    if src.endswith(".cu"):
+        f += ARCH + ["--expt-relaxed-constexpr", "-Xptxas", "-v"] if os.environ.get("DFMM_PTXAS_V") else ARCH
+    else:
+        # host code: no FMA contraction, so the skeleton arithmetic is reproducible
+        f += ["-x", "cu", "-Xcompiler", "-ffp-contract=off"] + ARCH
+    return f
+
+
+def build(verbose: bool = False) -> str:
+    os.makedirs(BUILD, exist_ok=True)
+    srcs = [s for s in SOURCES if os.path.exists(os.path.join(CSRC, s))]
+    objs = []
+    cmds = []
+    for s in srcs:
+        o = os.path.join(BUILD, s + ".o")
+        objs.append(o)
+        src = os.path.join(CSRC, s)
+        deps = [src] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
+        deps.append(os.path.join(INCLUDE, "dfmm.h"))
+        if os.path.exists(o) and all(os.path.getmtime(o) >= os.path.getmtime(d) for d in deps):
+            continue
+        cmds.append([nvcc(), "-c", src, "-o", o] + _flags(s))
+    errs = []
+    with cf.ThreadPoolExecutor(max_workers=min(8, max(1, len(cmds)))) as ex:
+        for cmd, res in zip(cmds, ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), cmds)):
+            if verbose or res.returncode != 0:
+                sys.stderr.write(" ".join(cmd) + "\n" + res.stdout + res.stderr)
+            if res.returncode != 0:
+                errs.append(cmd[2])
+    if errs:
+        raise RuntimeError("nvcc failed for: " + ", ".join(errs))
+    if cmds or not os.path.exists(LIB):
+        link = [nvcc(), "-shared", "-o", LIB] + objs + ARCH + ["-lcublas", "-lcudart"]
+        res = subprocess.run(link, capture_output=True, text=True)
+        if res.returncode != 0:
+            raise RuntimeError("link failed:\n" + res.stdout + res.stderr)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(verbose="-v" in sys.argv))

@@ -1,0 +1,80 @@
+// Apply-time kernels of the matvec (see apply.cu).
+#pragma once
+#include <cstdint>
+
+#include "common.h"
+
+namespace dfmm {
+
+// Check point of an LF representation, for kernel evaluation with a
+// compensated phase: x = local point, nx2 = |x|^2, nx = |x|, fx = frac(|x|).
+struct ChkPt {
+  float x, y, z, nx2;
+  float nx, fx, pad0, pad1;
+};
+
+// One translation stage: y[dst] += T_op x[src] for every (src, dst) pair,
+// columns = pairs x nrhs.  Operators complex64 [nops][M][Kd] row-major.
+struct GemmArgs {
+  const float2* ops;
+  int M, Kd;
+  const int4* tiles;        // (op, first pair, number of pairs, 0)
+  int64_t ntiles;
+  const int2* pairs;        // (src row, dst row)
+  const float2* src;        // rows of src_ld complex, row index = src_row * nrhs + rhs
+  float2* dst;              // rows of dst_ld complex
+  int src_ld, dst_ld;
+  int nrhs;
+};
+
+void launch_gemm_stage(const GemmArgs& a, cudaStream_t s);
+
+// Permutes: fs[k][rhs] = f[rhs][perm[k]];  u[rhs][perm[k]] = us[k][rhs].
+void launch_permute_in(const float2* f, const int32_t* perm, int64_t N, int nrhs, float2* fs, cudaStream_t s);
+void launch_permute_out(const float2* us, const int32_t* perm, int64_t N, int nrhs, float2* u, cudaStream_t s);
+
+// Kernel evaluation from points to check points (P2M, and P2L with the
+// target box's check points): out[row][rhs][p] = sum_i G(c + x_p - y_i) f_i.
+// jobs: (first point, count, row, ptsrc shift index) ; shifts: float4 c_tgt - c_src
+// (zero for P2M).  pts: local coordinates relative to the source leaf centre.
+struct P2CArgs {
+  const int4* jobs;          // (first point, count, out row, shift index)
+  int64_t njobs;
+  const float4* shifts;      // (dx, dy, dz, 0): check-point frame minus point frame
+  const ChkPt* chk;          // 2r check points
+  int nchk, ld;              // number of check points, out row length (2R)
+  const float4* pts;         // sorted local points (x, y, z, |x|^2)
+  const float2* fs;          // [N][nrhs]
+  float2* out;               // [rows][nrhs][ld]
+  int nrhs;
+};
+void launch_p2c(const P2CArgs& a, cudaStream_t s);
+
+// Rows applied to states: us[i][rhs] += sum_q rows[row_i][q] state[srow][rhs][q].
+struct RowsArgs {
+  const int4* jobs;          // (first point, count, first row, state row)
+  int64_t njobs;
+  const float2* rows;        // [..][R]
+  const float2* state;       // [..][nrhs][R]
+  int R, nrhs;
+  float2* us;                // [N][nrhs]
+  int atomic;
+};
+void launch_rows(const RowsArgs& a, cudaStream_t s);
+
+// Near field: us[i] += sum over U-list source leaves of G(p_i, p_j) f_j,
+// skipping p_j == p_i.
+struct P2PArgs {
+  const int2* leaf_range;    // (first, count) per target leaf
+  int64_t nleaves;
+  const int64_t* u_off;      // CSR offsets per target leaf
+  const int4* u_src;         // (first, count, shift index, 0) per source leaf
+  const float4* shifts;      // c_src - c_tgt
+  const float4* pts;         // local (x, y, z, |x|^2)
+  const float2* fs;
+  float2* us;
+  int nrhs;
+};
+void launch_p2p(const P2PArgs& a, cudaStream_t s);
+
+}  // namespace dfmm

@@ -1,0 +1,1210 @@
+// C ABI of the directional FMM (include/dfmm.h): plan construction and the
+// apply sequence of Alg. 1 plus the near field.
+//
+// Plan: Morton keys, radix sort, octree and list enumeration run on the
+// device (sort.cu, tree.cu); the host groups the lists into per-operator work
+// tables, builds the representations (skeleton.cpp) and the device forms the
+// operators in FP64 (operators.cu).
+// Apply (one stream, no host synchronisation): permute in, P2M, LF-M2M,
+// HF-M2M, HF-L2L + HF-M2L per level, HF->LF L2L, LF-M2L (V), P2L (X), LF-L2L,
+// L2P, M2P (W), P2P (U), permute out.
+#include "dfmm.h"
+
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "apply.h"
+#include "common.h"
+#include "operators.h"
+#include "skeleton.h"
+#include "tree.h"
+
+using namespace dfmm;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+struct GemmPlan {
+  int M = 0, Kd = 0, nops = 0;
+  float2* ops = nullptr;
+  std::vector<int4> groups;        // (op, first pair, count, 0)
+  int2* pairs = nullptr;
+  int64_t npairs = 0;
+};
+
+struct HFLevel {
+  int l = 0;
+  double w = 0;
+  int n = 0, nd = 0, R = 0;
+  std::vector<int32_t> out_keys, in_keys;       // box * nd + dir, ascending
+  std::vector<int32_t> out_map, in_map;         // dense -> slot (-1 if inactive)
+  std::vector<int> out_cells, in_cells;         // distinct active directions
+  PairList pairs;
+  GemmPlan m2m, m2l, l2l;   // into this level: M2M from l+1, M2L, L2L from l-1
+};
+
+struct LFLevel {
+  int l = 0;
+  double w = 0;
+  int R = 0, r = 0;
+  int64_t nbox = 0;
+  GemmPlan m2m, l2l, v, p2m, p2l;   // m2m from l+1, l2l from l-1 (LF or HF)
+  ChkPt* chk_a2 = nullptr;
+  ChkPt* chk_b2 = nullptr;
+  int4* p2m_jobs = nullptr;
+  int64_t n_p2m = 0;
+  int4* p2l_jobs = nullptr;
+  float4* p2l_shifts = nullptr;
+  int64_t n_p2l = 0;
+  int4* l2p_jobs = nullptr;
+  int64_t n_l2p = 0;
+  float2* l2p_rows = nullptr;
+};
+
+struct M2PGroup {
+  int src_level = 0;
+  int R = 0;
+  int4* jobs = nullptr;
+  int64_t njobs = 0;
+  float2* rows = nullptr;
+};
+
+struct Workspace {
+  int nrhs = 0;
+  DevArena ar;
+  float2 *fs = nullptr, *us = nullptr, *p2m = nullptr, *p2l = nullptr;
+  std::vector<float2*> S, T;                            // per level (LF or HF states)
+  std::vector<std::pair<void*, size_t>> zero;           // reset before each apply
+  std::map<std::pair<const void*, int>, std::pair<int4*, int64_t>> tiles;
+  float2 *f_dev = nullptr, *u_dev = nullptr;            // staging for host applies
+  unsigned* status = nullptr;
+};
+
+}  // namespace
+
+struct dfmm_plan_s {
+  int device = 0;
+  int64_t N = 0;
+  double K = 0, W = 0, eps = 0, eps_op = 0;
+  dfmm_options opt{};
+  DevArena ar;
+  TreeBuilder tree;
+  int32_t* perm = nullptr;
+  std::vector<int32_t> h_perm;
+  std::vector<uint64_t> h_keys;
+  float4* pts_local = nullptr;
+  int l1 = -1, l_top = -1, l_lf0 = -1, nl = 0;
+  std::vector<HFLevel> hf;
+  std::vector<LFLevel> lf;
+  std::vector<PairList> vlist;
+  std::vector<int32_t> U, Wl, X;
+  std::vector<M2PGroup> m2p;
+  int2* p2p_range = nullptr;
+  int64_t* p2p_off = nullptr;
+  int4* p2p_src = nullptr;
+  float4* p2p_shift = nullptr;
+  int64_t n_leaves = 0;
+  float4* zero_shift = nullptr;
+  std::unique_ptr<RepSet> reps;
+  std::vector<std::array<int64_t, 3>> rep_ranks;   // (level, cell, rank)
+  dfmm_stats stats{};
+  std::mutex ws_mu;
+  std::map<cudaStream_t, std::unique_ptr<Workspace>> ws;
+};
+
+namespace {
+
+double now() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+std::vector<int32_t> near_template(double w) {
+  int R = (int)std::ceil(w) + 1;
+  int64_t lim = std::llround(4 * w * w);
+  std::vector<int32_t> t;
+  for (int x = -R; x <= R; ++x)
+    for (int y = -R; y <= R; ++y)
+      for (int z = -R; z <= R; ++z) {
+        int64_t a = std::max(0, 2 * std::abs(x) - 1), b = std::max(0, 2 * std::abs(y) - 1),
+                c = std::max(0, 2 * std::abs(z) - 1);
+        if (a * a + b * b + c * c <= lim) { t.push_back(x); t.push_back(y); t.push_back(z); }
+      }
+  return t;
+}
+
+std::vector<int32_t> colleague_template() {
+  std::vector<int32_t> t;
+  for (int x = -1; x <= 1; ++x)
+    for (int y = -1; y <= 1; ++y)
+      for (int z = -1; z <= 1; ++z) { t.push_back(x); t.push_back(y); t.push_back(z); }
+  return t;
+}
+
+// Fig. 2 hierarchy: cell (f, i, j) of the parent grid lies in (f, i/2, j/2).
+int parent_cell(int d, int n_parent) {
+  int f = d / (n_parent * n_parent), rem = d % (n_parent * n_parent);
+  int i = rem / n_parent, j = rem % n_parent;
+  int nc = n_parent / 2;
+  return (f * nc + i / 2) * nc + j / 2;
+}
+
+int octant_of(const int32_t* c) { return ((c[0] & 1) << 2) | ((c[1] & 1) << 1) | (c[2] & 1); }
+
+// c_child - c_parent for octant o
+void octant_delta(int o, double w_child, double out[3]) {
+  out[0] = (((o >> 2) & 1) - 0.5) * w_child;
+  out[1] = (((o >> 1) & 1) - 0.5) * w_child;
+  out[2] = ((o & 1) - 0.5) * w_child;
+}
+
+// (op, src, dst) triples -> GemmPlan with pairs grouped by operator
+void finish_gemm(GemmPlan& g, const std::vector<int32_t>& op, const std::vector<int2>& pr, DevArena& ar,
+                 cudaStream_t s) {
+  int64_t n = (int64_t)op.size();
+  g.npairs = n;
+  g.groups.clear();
+  if (n == 0) return;
+  std::vector<int64_t> cnt(g.nops + 1, 0);
+  for (int64_t i = 0; i < n; ++i) cnt[op[i] + 1]++;
+  for (int k = 0; k < g.nops; ++k) cnt[k + 1] += cnt[k];
+  std::vector<int2> sorted(n);
+  std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+  for (int64_t i = 0; i < n; ++i) sorted[pos[op[i]]++] = pr[i];
+  for (int k = 0; k < g.nops; ++k)
+    if (cnt[k + 1] > cnt[k]) g.groups.push_back(make_int4(k, (int)cnt[k], (int)(cnt[k + 1] - cnt[k]), 0));
+  g.pairs = ar.alloc<int2>(n);
+  DFMM_CUDA(cudaMemcpyAsync(g.pairs, sorted.data(), n * sizeof(int2), cudaMemcpyHostToDevice, s));
+  DFMM_CUDA(cudaStreamSynchronize(s));
+}
+
+template <class T>
+T* upload(const std::vector<T>& v, DevArena& ar, cudaStream_t s) {
+  T* d = ar.alloc<T>(std::max<size_t>(1, v.size()));
+  if (!v.empty()) DFMM_CUDA(cudaMemcpyAsync(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  DFMM_CUDA(cudaStreamSynchronize(s));
+  return d;
+}
+
+// conjugate transpose of a 2r x r matrix, columns scaled, padded to R x 2R, complex64
+float2* upload_projection(const std::vector<cd>& Q, int r, const double* colscale, int R, DevArena& ar,
+                          cudaStream_t s) {
+  std::vector<float2> h((size_t)R * 2 * R, make_float2(0, 0));
+  for (int i = 0; i < r; ++i)
+    for (int j = 0; j < 2 * r; ++j) {
+      cd v = std::conj(Q[(size_t)j * r + i]);
+      if (colscale) v *= colscale[j];
+      h[(size_t)i * 2 * R + j] = make_float2((float)v.real(), (float)v.imag());
+    }
+  return upload(h, ar, s);
+}
+
+ChkPt* upload_chk(const std::vector<double>& pts, int n, DevArena& ar, cudaStream_t s) {
+  std::vector<ChkPt> h(n);
+  for (int p = 0; p < n; ++p) {
+    double x = pts[3 * p], y = pts[3 * p + 1], z = pts[3 * p + 2];
+    double n2 = x * x + y * y + z * z, nn = std::sqrt(n2);
+    h[p].x = (float)x; h[p].y = (float)y; h[p].z = (float)z;
+    h[p].nx2 = (float)n2;
+    h[p].nx = (float)nn;
+    h[p].fx = (float)(nn - std::floor(nn));
+    h[p].pad0 = h[p].pad1 = 0.f;
+  }
+  return upload(h, ar, s);
+}
+
+void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
+  double t0 = now();
+  const int64_t N = P->N;
+  DevArena& ar = P->ar;
+  // ---- host copy of the points, domain check
+  std::vector<double> hp((size_t)N * 3);
+  DFMM_CUDA(cudaMemcpy(hp.data(), d_points, N * 24, cudaMemcpyDeviceToHost));
+  for (int64_t i = 0; i < 3 * N; ++i)
+    if (!(std::fabs(hp[i]) <= 0.5 * P->K))
+      throw Error(DFMM_ERR_DOMAIN, "point " + std::to_string(i / 3) + " lies outside |x|_inf <= K/2");
+  // ---- Morton keys and stable radix sort (device)
+  uint64_t* keys = ar.alloc<uint64_t>(N);
+  P->perm = ar.alloc<int32_t>(N);
+  {
+    ArenaMark mk(ar);
+    double* dp = ar.alloc<double>(3 * N);
+    DFMM_CUDA(cudaMemcpyAsync(dp, d_points, N * 24, cudaMemcpyDeviceToDevice, s));
+    uint64_t* k2 = ar.alloc<uint64_t>(N);
+    int32_t* v2 = ar.alloc<int32_t>(N);
+    size_t sb = radix_sort_scratch_bytes(N);
+    void* scratch = ar.alloc<char>(sb);
+    launch_morton_keys(dp, N, P->W, keys, P->perm, s);
+    radix_sort_pairs(keys, P->perm, k2, v2, N, 63, scratch, sb, s);
+    DFMM_CUDA(cudaStreamSynchronize(s));
+  }
+  P->h_perm.resize(N);
+  P->h_keys.resize(N);
+  DFMM_CUDA(cudaMemcpy(P->h_perm.data(), P->perm, N * 4, cudaMemcpyDeviceToHost));
+  DFMM_CUDA(cudaMemcpy(P->h_keys.data(), keys, N * 8, cudaMemcpyDeviceToHost));
+  // ---- octree (device)
+  TreeBuilder& T = P->tree;
+  T.build(keys, N, P->W, P->opt.leaf_max, s, ar);
+  const int nl = (int)T.levels.size();
+  const std::vector<TreeLevel>& LV = T.levels;
+  P->nl = nl;
+  P->stats.n_levels = nl;
+  for (int l = 0; l < nl && l < 32; ++l) {
+    P->stats.boxes[l] = LV[l].n;
+    int64_t nleaf = 0;
+    for (auto v : LV[l].h_leaf) nleaf += v;
+    P->stats.leaves[l] = nleaf;
+  }
+  P->l1 = (int)std::llround(std::log2(P->W));
+  P->stats.level_w1 = P->l1;
+  P->l_lf0 = P->l1 + 1;
+  if (P->l_lf0 >= nl) throw Error(DFMM_ERR_INVALID, "octree has no low-frequency level");
+  unsigned* d_status = ar.alloc<unsigned>(1);
+  DFMM_CUDA(cudaMemsetAsync(d_status, 0, 4, s));
+  // ---- HF lists (device)
+  P->hf.resize(nl);
+  for (int l = 1; l <= P->l1; ++l) {
+    HFLevel& H = P->hf[l];
+    H.l = l;
+    H.w = LV[l].w;
+    H.n = n_cells(H.w);
+    H.nd = 6 * H.n * H.n;
+    // Prop. 1 with |p|_inf <= K/2: two data points are at most sqrt(3) K apart and
+    // a box centre lies within sqrt(3) w / 2 of one of its points, so for
+    // w^2 >= sqrt(3) (K + w / 2) every non-empty box is near and I^B is empty.
+    if (H.w * H.w >= std::sqrt(3.0) * (P->K + 0.5 * H.w)) continue;
+    H.pairs = T.pairs(l, near_template(2 * H.w), 0, std::llround(4 * H.w * H.w), true, H.n, s, ar);
+    if (H.pairs.n > 0 && P->l_top < 0) P->l_top = l;
+    P->stats.hf_pairs[l] = H.pairs.n;
+  }
+  P->stats.level_hf_top = P->l_top;
+  // ---- LF lists (device)
+  P->lf.resize(nl);
+  P->vlist.resize(nl);
+  for (int l = P->l_lf0; l < nl; ++l) {
+    P->vlist[l] = T.pairs(l, colleague_template(), 1, 0, false, 0, s, ar);
+    P->stats.v_pairs += P->vlist[l].n;
+  }
+  T.uw_lists(P->l_lf0, s, ar, P->U, P->Wl, d_status);
+  {
+    unsigned st = 0;
+    DFMM_CUDA(cudaMemcpy(&st, d_status, 4, cudaMemcpyDeviceToHost));
+    if (st) throw Error(DFMM_ERR_DEVICE, "list construction overflowed its descent stack");
+  }
+  const size_t nU = P->U.size() / 4, nW = P->Wl.size() / 4;
+  P->X.resize(4 * nW);
+  for (size_t q = 0; q < nW; ++q) {
+    P->X[4 * q] = P->Wl[4 * q + 2];
+    P->X[4 * q + 1] = P->Wl[4 * q + 3];
+    P->X[4 * q + 2] = P->Wl[4 * q];
+    P->X[4 * q + 3] = P->Wl[4 * q + 1];
+  }
+  P->stats.u_pairs = (int64_t)nU;
+  P->stats.w_pairs = (int64_t)nW;
+  P->stats.x_pairs = (int64_t)nW;
+  // ---- active directions (closure under the wedge hierarchy)
+  const bool has_hf = P->l_top >= 0;
+  if (has_hf) {
+    for (int l = P->l_top; l <= P->l1; ++l) {
+      HFLevel& H = P->hf[l];
+      const TreeLevel& L = LV[l];
+      std::vector<uint8_t> fo((size_t)L.n * H.nd, 0), fi((size_t)L.n * H.nd, 0);
+      for (int64_t q = 0; q < H.pairs.n; ++q) {
+        fo[(size_t)H.pairs.src[q] * H.nd + H.pairs.dout[q]] = 1;
+        fi[(size_t)H.pairs.tgt[q] * H.nd + H.pairs.din[q]] = 1;
+      }
+      if (l > P->l_top) {
+        const HFLevel& Hp = P->hf[l - 1];
+        const TreeLevel& Lp = LV[l - 1];
+        for (int pass = 0; pass < 2; ++pass) {
+          const std::vector<int32_t>& kp = pass == 0 ? Hp.out_keys : Hp.in_keys;
+          std::vector<uint8_t>& f = pass == 0 ? fo : fi;
+          for (int32_t key : kp) {
+            int pb = key / Hp.nd, pd = key % Hp.nd;
+            int cd = parent_cell(pd, Hp.n);
+            for (int k = 0; k < Lp.h_nchild[pb]; ++k) f[(size_t)(Lp.h_child_first[pb] + k) * H.nd + cd] = 1;
+          }
+        }
+      }
+      H.out_map.assign(fo.size(), -1);
+      H.in_map.assign(fi.size(), -1);
+      std::vector<uint8_t> co(H.nd, 0), ci(H.nd, 0);
+      for (size_t k = 0; k < fo.size(); ++k) {
+        if (fo[k]) { H.out_map[k] = (int32_t)H.out_keys.size(); H.out_keys.push_back((int32_t)k); co[k % H.nd] = 1; }
+        if (fi[k]) { H.in_map[k] = (int32_t)H.in_keys.size(); H.in_keys.push_back((int32_t)k); ci[k % H.nd] = 1; }
+      }
+      for (int d = 0; d < H.nd; ++d) {
+        if (co[d]) H.out_cells.push_back(d);
+        if (ci[d]) H.in_cells.push_back(d);
+      }
+      P->stats.slots_out[l] = (int64_t)H.out_keys.size();
+      P->stats.slots_in[l] = (int64_t)H.in_keys.size();
+    }
+  }
+  // ---- representations (host skeletons, built in parallel)
+  double w_top = has_hf ? LV[P->l_top].w : 1.0;
+  SkelParams sp;
+  sp.eps_op = P->eps_op;
+  sp.S_Y = P->opt.sample_box;
+  sp.S_X = P->opt.sample_far;
+  sp.sketch = P->opt.sketch_rows;
+  P->reps.reset(new RepSet(sp, w_top, P->opt.host_threads, P->opt.cache_dir ? P->opt.cache_dir : ""));
+  std::vector<std::vector<int>> level_cells(nl);
+  std::vector<std::pair<double, int>> need;
+  for (int l = (has_hf ? P->l_top : P->l_lf0); l < nl; ++l) {
+    if (l <= P->l1) {
+      std::vector<uint8_t> used(P->hf[l].nd, 0);
+      for (int d : P->hf[l].out_cells) used[d] = 1;
+      for (int d : P->hf[l].in_cells) used[d] = 1;
+      for (int d = 0; d < P->hf[l].nd; ++d) if (used[d]) level_cells[l].push_back(d);
+    } else {
+      level_cells[l].push_back(-1);
+    }
+    for (int c : level_cells[l]) need.push_back({LV[l].w, c});
+  }
+  P->reps->prepare(need);
+  std::vector<DevRep> dreps;
+  std::map<std::pair<int, int>, int> ridx;   // (level, cell) -> dreps index
+  for (int l = (has_hf ? P->l_top : P->l_lf0); l < nl; ++l) {
+    int rmax = 0;
+    for (int c : level_cells[l]) rmax = std::max(rmax, P->reps->get(LV[l].w, c).r);
+    int R = round_up(std::max(rmax, 4), 4);
+    if (R > 256) throw Error(DFMM_ERR_UNSUPPORTED, "representation rank above 256");
+    if (l <= P->l1) P->hf[l].R = R;
+    else { P->lf[l].R = R; P->lf[l].r = rmax; }
+    P->stats.rank[l] = R;
+    for (int c : level_cells[l]) {
+      const Rep& rp = P->reps->get(LV[l].w, c);
+      ridx[{l, c}] = (int)dreps.size();
+      dreps.push_back(upload_rep(rp, R, ar, s));
+      P->rep_ranks.push_back({(int64_t)l, (int64_t)c, (int64_t)rp.r});
+    }
+  }
+  cublasHandle_t cb;
+  if (cublasCreate(&cb) != CUBLAS_STATUS_SUCCESS) throw Error(DFMM_ERR_CUDA, "cublasCreate failed");
+  struct CbGuard { cublasHandle_t h; ~CbGuard() { cublasDestroy(h); } } cbg{cb};
+  double m2l_flops = 0, other_flops = 0;
+  auto center = [&](int l, int64_t b, int d) { return -0.5 * P->W + (LV[l].h_coords[3 * b + d] + 0.5) * LV[l].w; };
+  P->zero_shift = upload(std::vector<float4>{make_float4(0, 0, 0, 0)}, ar, s);
+
+  // ---- LF levels
+  for (int l = P->l_lf0; l < nl; ++l) {
+    LFLevel& F = P->lf[l];
+    F.l = l;
+    F.w = LV[l].w;
+    F.nbox = LV[l].n;
+    const Rep& rp = P->reps->get(F.w, -1);
+    const int R = F.R;
+    F.chk_a2 = upload_chk(rp.a2, 2 * rp.r, ar, s);
+    F.chk_b2 = upload_chk(rp.b2, 2 * rp.r, ar, s);
+    F.p2m.M = R; F.p2m.Kd = 2 * R; F.p2m.nops = 1;
+    F.p2m.ops = upload_projection(rp.Qo, rp.r, rp.wa2.data(), R, ar, s);
+    F.p2l.M = R; F.p2l.Kd = 2 * R; F.p2l.nops = 1;
+    F.p2l.ops = upload_projection(rp.Qi, rp.r, nullptr, R, ar, s);
+    std::vector<int4> jobs;
+    std::vector<int32_t> op;
+    std::vector<int2> pr;
+    // P2M: leaves of this level
+    for (int64_t b = 0; b < LV[l].n; ++b)
+      if (LV[l].h_leaf[b]) {
+        jobs.push_back(make_int4(LV[l].h_first[b], LV[l].h_count[b], (int)jobs.size(), 0));
+        op.push_back(0);
+        pr.push_back(make_int2((int)jobs.size() - 1, (int)b));
+      }
+    F.n_p2m = (int64_t)jobs.size();
+    F.p2m_jobs = upload(jobs, ar, s);
+    finish_gemm(F.p2m, op, pr, ar, s);
+    other_flops += 8.0 * rp.r * 2 * rp.r * F.n_p2m;
+    // P2L: X pairs whose target is at this level
+    {
+      std::vector<int4> xj;
+      std::vector<float4> xs;
+      op.clear(); pr.clear();
+      for (size_t q = 0; q < nW; ++q) {
+        int lb = P->X[4 * q], b = P->X[4 * q + 1], la = P->X[4 * q + 2], a = P->X[4 * q + 3];
+        if (lb != l) continue;
+        float sh[3];
+        for (int d = 0; d < 3; ++d) sh[d] = (float)(center(la, a, d) - center(lb, b, d));
+        xs.push_back(make_float4(sh[0], sh[1], sh[2], 0.f));
+        xj.push_back(make_int4(LV[la].h_first[a], LV[la].h_count[a], (int)xj.size(), (int)xs.size() - 1));
+        op.push_back(0);
+        pr.push_back(make_int2((int)xj.size() - 1, b));
+      }
+      F.n_p2l = (int64_t)xj.size();
+      F.p2l_jobs = upload(xj, ar, s);
+      F.p2l_shifts = upload(xs, ar, s);
+      finish_gemm(F.p2l, op, pr, ar, s);
+    }
+    // LF-M2L over the V list: one operator per offset
+    {
+      const PairList& V = P->vlist[l];
+      std::map<std::array<int, 3>, int> offs;
+      std::vector<OpSpec> specs;
+      op.clear(); pr.clear();
+      for (int64_t q = 0; q < V.n; ++q) {
+        std::array<int, 3> m = {V.m[3 * q], V.m[3 * q + 1], V.m[3 * q + 2]};
+        auto it = offs.find(m);
+        int id;
+        if (it == offs.end()) {
+          id = (int)specs.size();
+          offs[m] = id;
+          OpSpec o;
+          o.tgt_rep = o.src_rep = ridx.at({l, -1});
+          for (int d = 0; d < 3; ++d) o.shift[d] = -F.w * m[d];
+          specs.push_back(o);
+        } else id = it->second;
+        op.push_back(id);
+        pr.push_back(make_int2(V.src[q], V.tgt[q]));
+      }
+      F.v.M = R; F.v.Kd = R; F.v.nops = (int)specs.size();
+      if (!specs.empty()) {
+        F.v.ops = ar.alloc<float2>((size_t)specs.size() * R * R);
+        form_ops(kOpM2L, specs, dreps, R, R, F.v.ops, cb, ar, s);
+      }
+      finish_gemm(F.v, op, pr, ar, s);
+      m2l_flops += 8.0 * rp.r * rp.r * V.n;
+    }
+    // LF-M2M from level l+1 (LF children) and LF-L2L from level l-1 (LF parent)
+    if (l + 1 < nl) {
+      const LFLevel& C = P->lf[l + 1];
+      const TreeLevel& Lc = LV[l + 1];
+      std::vector<OpSpec> specs(8);
+      for (int o = 0; o < 8; ++o) {
+        double dl[3];
+        octant_delta(o, Lc.w, dl);
+        specs[o].tgt_rep = ridx.at({l, -1});
+        specs[o].src_rep = ridx.at({l + 1, -1});
+        for (int d = 0; d < 3; ++d) specs[o].shift[d] = -dl[d];
+      }
+      int Rc = P->lf[l + 1].R;
+      (void)C;
+      F.m2m.M = R; F.m2m.Kd = Rc; F.m2m.nops = 8;
+      F.m2m.ops = ar.alloc<float2>((size_t)8 * R * Rc);
+      form_ops(kOpM2M, specs, dreps, R, Rc, F.m2m.ops, cb, ar, s);
+      op.clear(); pr.clear();
+      for (int64_t c = 0; c < Lc.n; ++c) {
+        op.push_back(octant_of(&Lc.h_coords[3 * c]));
+        pr.push_back(make_int2((int)c, Lc.h_parent[c]));
+      }
+      finish_gemm(F.m2m, op, pr, ar, s);
+      other_flops += 8.0 * R * Rc * Lc.n;
+    }
+    if (l > P->l_lf0) {
+      const TreeLevel& Lp = LV[l - 1];
+      const int Rp = P->lf[l - 1].R;
+      std::vector<OpSpec> specs(8);
+      for (int o = 0; o < 8; ++o) {
+        double dl[3];
+        octant_delta(o, F.w, dl);
+        specs[o].tgt_rep = ridx.at({l, -1});
+        specs[o].src_rep = ridx.at({l - 1, -1});
+        for (int d = 0; d < 3; ++d) specs[o].shift[d] = dl[d];
+      }
+      F.l2l.M = R; F.l2l.Kd = Rp; F.l2l.nops = 8;
+      F.l2l.ops = ar.alloc<float2>((size_t)8 * R * Rp);
+      form_ops(kOpL2L, specs, dreps, R, Rp, F.l2l.ops, cb, ar, s);
+      op.clear(); pr.clear();
+      for (int64_t c = 0; c < LV[l].n; ++c) {
+        op.push_back(octant_of(&LV[l].h_coords[3 * c]));
+        pr.push_back(make_int2(LV[l].h_parent[c], (int)c));
+      }
+      finish_gemm(F.l2l, op, pr, ar, s);
+      other_flops += 8.0 * R * Rp * LV[l].n;
+      (void)Lp;
+    }
+  }
+
+  // ---- HF levels
+  if (has_hf) {
+    for (int l = P->l_top; l <= P->l1; ++l) {
+      HFLevel& H = P->hf[l];
+      const TreeLevel& L = LV[l];
+      const int R = H.R;
+      std::vector<int32_t> op;
+      std::vector<int2> pr;
+      // HF-M2L, one operator per offset m
+      {
+        std::unordered_map<int64_t, int> offs;
+        std::vector<OpSpec> specs;
+        const PairList& Pp = H.pairs;
+        int64_t Rm = 8 * (int64_t)std::ceil(H.w) + 8;
+        for (int64_t q = 0; q < Pp.n; ++q) {
+          int64_t m0 = Pp.m[3 * q], m1 = Pp.m[3 * q + 1], m2 = Pp.m[3 * q + 2];
+          int64_t key = ((m0 + Rm) * (2 * Rm + 1) + (m1 + Rm)) * (2 * Rm + 1) + (m2 + Rm);
+          auto it = offs.find(key);
+          int id;
+          if (it == offs.end()) {
+            id = (int)specs.size();
+            offs.emplace(key, id);
+            OpSpec o;
+            o.tgt_rep = ridx.at({l, Pp.din[q]});
+            o.src_rep = ridx.at({l, Pp.dout[q]});
+            o.shift[0] = -H.w * m0; o.shift[1] = -H.w * m1; o.shift[2] = -H.w * m2;
+            specs.push_back(o);
+          } else id = it->second;
+          op.push_back(id);
+          int ss = H.out_map[(size_t)Pp.src[q] * H.nd + Pp.dout[q]];
+          int ts = H.in_map[(size_t)Pp.tgt[q] * H.nd + Pp.din[q]];
+          pr.push_back(make_int2(ss, ts));
+          m2l_flops += 8.0 * P->reps->get(H.w, Pp.din[q]).r * P->reps->get(H.w, Pp.dout[q]).r;
+        }
+        P->stats.hf_offsets[l] = (int64_t)specs.size();
+        H.m2l.M = R; H.m2l.Kd = R; H.m2l.nops = (int)specs.size();
+        if (!specs.empty()) {
+          H.m2l.ops = ar.alloc<float2>((size_t)specs.size() * R * R);
+          form_ops(kOpM2L, specs, dreps, R, R, H.m2l.ops, cb, ar, s);
+        }
+        finish_gemm(H.m2l, op, pr, ar, s);
+      }
+      // HF-M2M into this level from its children (level l+1: HF or, at w = 1, LF)
+      {
+        const bool child_lf = (l == P->l1);
+        const TreeLevel& Lc = LV[l + 1];
+        const int Rc = child_lf ? P->lf[l + 1].R : P->hf[l + 1].R;
+        std::vector<int> cell_id(H.nd, -1);
+        for (size_t k = 0; k < H.out_cells.size(); ++k) cell_id[H.out_cells[k]] = (int)k;
+        std::vector<OpSpec> specs;
+        for (int d : H.out_cells)
+          for (int o = 0; o < 8; ++o) {
+            double dl[3];
+            octant_delta(o, Lc.w, dl);
+            OpSpec sp2;
+            sp2.tgt_rep = ridx.at({l, d});
+            sp2.src_rep = child_lf ? ridx.at({l + 1, -1}) : ridx.at({l + 1, parent_cell(d, H.n)});
+            for (int q = 0; q < 3; ++q) sp2.shift[q] = -dl[q];
+            specs.push_back(sp2);
+          }
+        H.m2m.M = R; H.m2m.Kd = Rc; H.m2m.nops = (int)specs.size();
+        H.m2m.ops = ar.alloc<float2>(std::max<size_t>(1, specs.size()) * R * Rc);
+        form_ops(kOpM2M, specs, dreps, R, Rc, H.m2m.ops, cb, ar, s);
+        op.clear(); pr.clear();
+        for (size_t k = 0; k < H.out_keys.size(); ++k) {
+          int b = H.out_keys[k] / H.nd, d = H.out_keys[k] % H.nd;
+          for (int c = 0; c < L.h_nchild[b]; ++c) {
+            int ch = L.h_child_first[b] + c;
+            int srow;
+            if (child_lf) srow = ch;
+            else {
+              const HFLevel& Hc = P->hf[l + 1];
+              srow = Hc.out_map[(size_t)ch * Hc.nd + parent_cell(d, H.n)];
+            }
+            op.push_back(cell_id[d] * 8 + octant_of(&Lc.h_coords[3 * ch]));
+            pr.push_back(make_int2(srow, (int)k));
+          }
+        }
+        finish_gemm(H.m2m, op, pr, ar, s);
+        other_flops += 8.0 * R * Rc * (double)op.size();
+      }
+      // HF-L2L into this level from its parent (l > l_top)
+      if (l > P->l_top) {
+        const HFLevel& Hp = P->hf[l - 1];
+        const TreeLevel& Lp = LV[l - 1];
+        std::vector<int> cell_id(Hp.nd, -1);
+        for (size_t k = 0; k < Hp.in_cells.size(); ++k) cell_id[Hp.in_cells[k]] = (int)k;
+        std::vector<OpSpec> specs;
+        for (int d : Hp.in_cells)
+          for (int o = 0; o < 8; ++o) {
+            double dl[3];
+            octant_delta(o, H.w, dl);
+            OpSpec sp2;
+            sp2.tgt_rep = ridx.at({l, parent_cell(d, Hp.n)});
+            sp2.src_rep = ridx.at({l - 1, d});
+            for (int q = 0; q < 3; ++q) sp2.shift[q] = dl[q];
+            specs.push_back(sp2);
+          }
+        H.l2l.M = R; H.l2l.Kd = Hp.R; H.l2l.nops = (int)specs.size();
+        H.l2l.ops = ar.alloc<float2>(std::max<size_t>(1, specs.size()) * R * Hp.R);
+        form_ops(kOpL2L, specs, dreps, R, Hp.R, H.l2l.ops, cb, ar, s);
+        op.clear(); pr.clear();
+        for (size_t k = 0; k < Hp.in_keys.size(); ++k) {
+          int b = Hp.in_keys[k] / Hp.nd, d = Hp.in_keys[k] % Hp.nd;
+          for (int c = 0; c < Lp.h_nchild[b]; ++c) {
+            int ch = Lp.h_child_first[b] + c;
+            int trow = H.in_map[(size_t)ch * H.nd + parent_cell(d, Hp.n)];
+            op.push_back(cell_id[d] * 8 + octant_of(&L.h_coords[3 * ch]));
+            pr.push_back(make_int2((int)k, trow));
+          }
+        }
+        finish_gemm(H.l2l, op, pr, ar, s);
+        other_flops += 8.0 * R * Hp.R * (double)op.size();
+      }
+    }
+    // HF-L2L from w = 1 into the LF incoming states (summed over directions)
+    {
+      const int l = P->l_lf0;
+      LFLevel& F = P->lf[l];
+      const HFLevel& Hp = P->hf[P->l1];
+      const TreeLevel& Lp = LV[P->l1];
+      std::vector<int> cell_id(Hp.nd, -1);
+      for (size_t k = 0; k < Hp.in_cells.size(); ++k) cell_id[Hp.in_cells[k]] = (int)k;
+      std::vector<OpSpec> specs;
+      for (int d : Hp.in_cells)
+        for (int o = 0; o < 8; ++o) {
+          double dl[3];
+          octant_delta(o, F.w, dl);
+          OpSpec sp2;
+          sp2.tgt_rep = ridx.at({l, -1});
+          sp2.src_rep = ridx.at({P->l1, d});
+          for (int q = 0; q < 3; ++q) sp2.shift[q] = dl[q];
+          specs.push_back(sp2);
+        }
+      F.l2l.M = F.R; F.l2l.Kd = Hp.R; F.l2l.nops = (int)specs.size();
+      F.l2l.ops = ar.alloc<float2>(std::max<size_t>(1, specs.size()) * F.R * Hp.R);
+      form_ops(kOpL2L, specs, dreps, F.R, Hp.R, F.l2l.ops, cb, ar, s);
+      std::vector<int32_t> op;
+      std::vector<int2> pr;
+      for (size_t k = 0; k < Hp.in_keys.size(); ++k) {
+        int b = Hp.in_keys[k] / Hp.nd, d = Hp.in_keys[k] % Hp.nd;
+        for (int c = 0; c < Lp.h_nchild[b]; ++c) {
+          int ch = Lp.h_child_first[b] + c;
+          op.push_back(cell_id[d] * 8 + octant_of(&LV[l].h_coords[3 * ch]));
+          pr.push_back(make_int2((int)k, ch));
+        }
+      }
+      finish_gemm(F.l2l, op, pr, ar, s);
+      other_flops += 8.0 * F.R * Hp.R * (double)op.size();
+    }
+  }
+
+  // ---- per-point data: local coordinates, L2P rows, P2P lists, M2P rows
+  std::vector<float4> loc(N);
+  std::vector<int> leaf_level(N, -1);
+  std::vector<int32_t> leaf_box(N, -1);
+  std::vector<int64_t> gleaf_of_box;    // not used directly
+  std::vector<int2> leaf_range;
+  std::map<std::pair<int, int>, int> gleaf;   // (level, box) -> global leaf id
+  std::vector<std::array<double, 3>> sorted_pts(N);
+  for (int64_t k = 0; k < N; ++k)
+    for (int d = 0; d < 3; ++d) sorted_pts[k][d] = hp[3 * (size_t)P->h_perm[k] + d];
+  for (int l = P->l_lf0; l < nl; ++l)
+    for (int64_t b = 0; b < LV[l].n; ++b) {
+      if (!LV[l].h_leaf[b]) continue;
+      gleaf[{l, (int)b}] = (int)leaf_range.size();
+      leaf_range.push_back(make_int2(LV[l].h_first[b], LV[l].h_count[b]));
+      double c[3] = {center(l, b, 0), center(l, b, 1), center(l, b, 2)};
+      for (int64_t i = LV[l].h_first[b]; i < LV[l].h_first[b] + LV[l].h_count[b]; ++i) {
+        double v[3] = {sorted_pts[i][0] - c[0], sorted_pts[i][1] - c[1], sorted_pts[i][2] - c[2]};
+        loc[i] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+        leaf_level[i] = l;
+        leaf_box[i] = (int32_t)b;
+      }
+    }
+  P->n_leaves = (int64_t)leaf_range.size();
+  P->pts_local = upload(loc, ar, s);
+  // L2P rows per LF level (FP64 local coordinates -> rows)
+  for (int l = P->l_lf0; l < nl; ++l) {
+    LFLevel& F = P->lf[l];
+    std::vector<double> lp;
+    std::vector<int4> jobs;
+    int64_t row = 0;
+    for (int64_t b = 0; b < LV[l].n; ++b) {
+      if (!LV[l].h_leaf[b]) continue;
+      double c[3] = {center(l, b, 0), center(l, b, 1), center(l, b, 2)};
+      jobs.push_back(make_int4(LV[l].h_first[b], LV[l].h_count[b], (int)row, (int)b));
+      for (int64_t i = LV[l].h_first[b]; i < LV[l].h_first[b] + LV[l].h_count[b]; ++i) {
+        for (int d = 0; d < 3; ++d) lp.push_back(sorted_pts[i][d] - c[d]);
+        ++row;
+      }
+    }
+    F.n_l2p = (int64_t)jobs.size();
+    F.l2p_jobs = upload(jobs, ar, s);
+    F.l2p_rows = ar.alloc<float2>(std::max<int64_t>(1, row) * F.R);
+    if (row > 0) {
+      ArenaMark mk(ar);
+      double* dlp = ar.alloc<double>(lp.size());
+      DFMM_CUDA(cudaMemcpyAsync(dlp, lp.data(), lp.size() * 8, cudaMemcpyHostToDevice, s));
+      form_rows(true, dreps[ridx.at({l, -1})], dlp, row, F.l2p_rows, cb, ar, s);
+    }
+    other_flops += 8.0 * F.r * (double)row;
+  }
+  // M2P rows (W list), grouped by the source level
+  for (int la = P->l_lf0; la < nl; ++la) {
+    std::vector<double> lp;
+    std::vector<int4> jobs;
+    int64_t row = 0;
+    for (size_t q = 0; q < nW; ++q) {
+      int lb = P->Wl[4 * q], b = P->Wl[4 * q + 1], l2 = P->Wl[4 * q + 2], a = P->Wl[4 * q + 3];
+      if (l2 != la) continue;
+      double c[3] = {center(la, a, 0), center(la, a, 1), center(la, a, 2)};
+      jobs.push_back(make_int4(LV[lb].h_first[b], LV[lb].h_count[b], (int)row, a));
+      for (int64_t i = LV[lb].h_first[b]; i < LV[lb].h_first[b] + LV[lb].h_count[b]; ++i) {
+        for (int d = 0; d < 3; ++d) lp.push_back(sorted_pts[i][d] - c[d]);
+        ++row;
+      }
+    }
+    if (jobs.empty()) continue;
+    M2PGroup g;
+    g.src_level = la;
+    g.R = P->lf[la].R;
+    g.njobs = (int64_t)jobs.size();
+    g.jobs = upload(jobs, ar, s);
+    g.rows = ar.alloc<float2>(row * g.R);
+    {
+      ArenaMark mk(ar);
+      double* dlp = ar.alloc<double>(lp.size());
+      DFMM_CUDA(cudaMemcpyAsync(dlp, lp.data(), lp.size() * 8, cudaMemcpyHostToDevice, s));
+      form_rows(false, dreps[ridx.at({la, -1})], dlp, row, g.rows, cb, ar, s);
+    }
+    P->m2p.push_back(g);
+  }
+  // P2P lists (U), CSR per target leaf with exact centre offsets
+  {
+    std::vector<std::vector<int4>> per(leaf_range.size());
+    std::vector<float4> shifts;
+    std::map<std::array<int64_t, 3>, int> shift_id;
+    double unit = LV[nl - 1].w / 2;   // all centre offsets are multiples of this
+    int64_t inter = 0;
+    for (size_t q = 0; q < nU; ++q) {
+      int lb = P->U[4 * q], b = P->U[4 * q + 1], la = P->U[4 * q + 2], a = P->U[4 * q + 3];
+      std::array<int64_t, 3> key;
+      double sh[3];
+      for (int d = 0; d < 3; ++d) {
+        sh[d] = center(la, a, d) - center(lb, b, d);
+        key[d] = std::llround(sh[d] / unit);
+      }
+      auto it = shift_id.find(key);
+      int sid;
+      if (it == shift_id.end()) {
+        sid = (int)shifts.size();
+        shift_id[key] = sid;
+        shifts.push_back(make_float4((float)sh[0], (float)sh[1], (float)sh[2], 0.f));
+      } else sid = it->second;
+      per[gleaf.at({lb, b})].push_back(make_int4(LV[la].h_first[a], LV[la].h_count[a], sid, 0));
+      inter += (int64_t)LV[lb].h_count[b] * LV[la].h_count[a];
+    }
+    std::vector<int64_t> off(leaf_range.size() + 1, 0);
+    std::vector<int4> src;
+    for (size_t g = 0; g < per.size(); ++g) {
+      off[g + 1] = off[g] + (int64_t)per[g].size();
+      src.insert(src.end(), per[g].begin(), per[g].end());
+    }
+    P->p2p_range = upload(leaf_range, ar, s);
+    P->p2p_off = upload(off, ar, s);
+    P->p2p_src = upload(src, ar, s);
+    P->p2p_shift = upload(shifts, ar, s);
+    P->stats.p2p_interactions = inter;
+  }
+  P->stats.m2l_flops = m2l_flops;
+  P->stats.other_translation_flops = other_flops;
+  P->stats.plan_bytes = (int64_t)ar.bytes();
+  P->stats.plan_seconds = now() - t0;
+}
+
+// ------------------------------------------------------------------- apply ---
+
+Workspace* get_workspace(dfmm_plan_s* P, cudaStream_t s, int nrhs) {
+  std::lock_guard<std::mutex> g(P->ws_mu);
+  auto& slot = P->ws[s];
+  if (slot && slot->nrhs >= nrhs) return slot.get();
+  slot.reset(new Workspace());
+  Workspace* W = slot.get();
+  W->nrhs = nrhs;
+  DevArena& ar = W->ar;
+  const int64_t N = P->N;
+  W->fs = ar.alloc<float2>(N * nrhs);
+  W->us = ar.alloc<float2>(N * nrhs);
+  W->zero.push_back({W->us, (size_t)N * nrhs * sizeof(float2)});
+  W->S.assign(P->nl, nullptr);
+  W->T.assign(P->nl, nullptr);
+  int64_t p2m_rows = 1, p2l_rows = 1;
+  for (int l = 0; l < P->nl; ++l) {
+    int64_t rows = 0;
+    int R = 0;
+    if (l >= P->l_lf0) { rows = P->lf[l].nbox; R = P->lf[l].R; }
+    else if (P->l_top >= 0 && l >= P->l_top) {
+      R = P->hf[l].R;
+      int64_t so = (int64_t)P->hf[l].out_keys.size(), si = (int64_t)P->hf[l].in_keys.size();
+      if (so) { W->S[l] = ar.alloc<float2>(so * nrhs * R); W->zero.push_back({W->S[l], (size_t)so * nrhs * R * 8}); }
+      if (si) { W->T[l] = ar.alloc<float2>(si * nrhs * R); W->zero.push_back({W->T[l], (size_t)si * nrhs * R * 8}); }
+      continue;
+    } else continue;
+    W->S[l] = ar.alloc<float2>(rows * nrhs * R);
+    W->T[l] = ar.alloc<float2>(rows * nrhs * R);
+    W->zero.push_back({W->S[l], (size_t)rows * nrhs * R * 8});
+    W->zero.push_back({W->T[l], (size_t)rows * nrhs * R * 8});
+    p2m_rows = std::max(p2m_rows, P->lf[l].n_p2m * 2 * R);
+    p2l_rows = std::max(p2l_rows, P->lf[l].n_p2l * 2 * R);
+  }
+  W->p2m = ar.alloc<float2>(p2m_rows * nrhs);
+  W->p2l = ar.alloc<float2>(p2l_rows * nrhs);
+  W->status = ar.alloc<unsigned>(1);
+  DFMM_CUDA(cudaMemsetAsync(W->status, 0, 4, s));
+  return W;
+}
+
+std::pair<int4*, int64_t> tiles_for(Workspace* W, const GemmPlan& g, int nrhs, cudaStream_t s) {
+  auto key = std::make_pair((const void*)&g, nrhs);
+  auto it = W->tiles.find(key);
+  if (it != W->tiles.end()) return it->second;
+  int per = std::max(1, 64 / nrhs);
+  std::vector<int4> t;
+  for (const int4& grp : g.groups)
+    for (int p = 0; p < grp.z; p += per) t.push_back(make_int4(grp.x, grp.y + p, std::min(per, grp.z - p), 0));
+  int4* d = W->ar.alloc<int4>(std::max<size_t>(1, t.size()));
+  if (!t.empty()) DFMM_CUDA(cudaMemcpyAsync(d, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+  W->tiles[key] = {d, (int64_t)t.size()};
+  return W->tiles[key];
+}
+
+void run_gemm(Workspace* W, const GemmPlan& g, const float2* src, int src_ld, float2* dst, int dst_ld, int nrhs,
+              cudaStream_t s) {
+  if (g.npairs == 0) return;
+  auto t = tiles_for(W, g, nrhs, s);
+  GemmArgs a;
+  a.ops = g.ops;
+  a.M = g.M;
+  a.Kd = g.Kd;
+  a.tiles = t.first;
+  a.ntiles = t.second;
+  a.pairs = g.pairs;
+  a.src = src;
+  a.dst = dst;
+  a.src_ld = src_ld;
+  a.dst_ld = dst_ld;
+  a.nrhs = nrhs;
+  launch_gemm_stage(a, s);
+}
+
+void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_t s) {
+  Workspace* W = get_workspace(P, s, nrhs);
+  // states are laid out for W->nrhs; use the caller's nrhs as the row stride
+  const int64_t N = P->N;
+  for (auto& z : W->zero) DFMM_CUDA(cudaMemsetAsync(z.first, 0, z.second, s));
+  launch_permute_in(f, P->perm, N, nrhs, W->fs, s);
+  const int nl = P->nl;
+  // 1. LF upward: P2M at leaves, LF-M2M from the level below
+  for (int l = nl - 1; l >= P->l_lf0; --l) {
+    LFLevel& F = P->lf[l];
+    if (F.n_p2m) {
+      P2CArgs a;
+      a.jobs = F.p2m_jobs;
+      a.njobs = F.n_p2m;
+      a.shifts = P->zero_shift;
+      a.chk = F.chk_a2;
+      a.nchk = 2 * F.r;
+      a.ld = 2 * F.R;
+      a.pts = P->pts_local;
+      a.fs = W->fs;
+      a.out = W->p2m;
+      a.nrhs = nrhs;
+      launch_p2c(a, s);
+      run_gemm(W, F.p2m, W->p2m, 2 * F.R, W->S[l], F.R, nrhs, s);
+    }
+    if (l + 1 < nl) run_gemm(W, F.m2m, W->S[l + 1], P->lf[l + 1].R, W->S[l], F.R, nrhs, s);
+  }
+  // 2. HF upward
+  if (P->l_top >= 0) {
+    for (int l = P->l1; l >= P->l_top; --l) {
+      HFLevel& H = P->hf[l];
+      const bool child_lf = (l == P->l1);
+      const float2* src = child_lf ? W->S[l + 1] : W->S[l + 1];
+      int sld = child_lf ? P->lf[l + 1].R : P->hf[l + 1].R;
+      run_gemm(W, H.m2m, src, sld, W->S[l], H.R, nrhs, s);
+    }
+    // 3. HF downward: L2L from the parent level, then M2L
+    for (int l = P->l_top; l <= P->l1; ++l) {
+      HFLevel& H = P->hf[l];
+      if (l > P->l_top) run_gemm(W, H.l2l, W->T[l - 1], P->hf[l - 1].R, W->T[l], H.R, nrhs, s);
+      run_gemm(W, H.m2l, W->S[l], H.R, W->T[l], H.R, nrhs, s);
+    }
+  }
+  // 4. LF downward
+  for (int l = P->l_lf0; l < nl; ++l) {
+    LFLevel& F = P->lf[l];
+    if (l == P->l_lf0) {
+      if (P->l_top >= 0) run_gemm(W, F.l2l, W->T[P->l1], P->hf[P->l1].R, W->T[l], F.R, nrhs, s);
+    } else {
+      run_gemm(W, F.l2l, W->T[l - 1], P->lf[l - 1].R, W->T[l], F.R, nrhs, s);
+    }
+    run_gemm(W, F.v, W->S[l], F.R, W->T[l], F.R, nrhs, s);
+    if (F.n_p2l) {
+      P2CArgs a;
+      a.jobs = F.p2l_jobs;
+      a.njobs = F.n_p2l;
+      a.shifts = F.p2l_shifts;
+      a.chk = F.chk_b2;
+      a.nchk = 2 * F.r;
+      a.ld = 2 * F.R;
+      a.pts = P->pts_local;
+      a.fs = W->fs;
+      a.out = W->p2l;
+      a.nrhs = nrhs;
+      launch_p2c(a, s);
+      run_gemm(W, F.p2l, W->p2l, 2 * F.R, W->T[l], F.R, nrhs, s);
+    }
+  }
+  // 5. L2P at every leaf, M2P over the W list
+  for (int l = P->l_lf0; l < nl; ++l) {
+    LFLevel& F = P->lf[l];
+    RowsArgs a;
+    a.jobs = F.l2p_jobs;
+    a.njobs = F.n_l2p;
+    a.rows = F.l2p_rows;
+    a.state = W->T[l];
+    a.R = F.R;
+    a.nrhs = nrhs;
+    a.us = W->us;
+    a.atomic = 0;
+    launch_rows(a, s);
+  }
+  for (auto& g : P->m2p) {
+    RowsArgs a;
+    a.jobs = g.jobs;
+    a.njobs = g.njobs;
+    a.rows = g.rows;
+    a.state = W->S[g.src_level];
+    a.R = g.R;
+    a.nrhs = nrhs;
+    a.us = W->us;
+    a.atomic = 1;
+    launch_rows(a, s);
+  }
+  // 6. near field
+  {
+    P2PArgs a;
+    a.leaf_range = P->p2p_range;
+    a.nleaves = P->n_leaves;
+    a.u_off = P->p2p_off;
+    a.u_src = P->p2p_src;
+    a.shifts = P->p2p_shift;
+    a.pts = P->pts_local;
+    a.fs = W->fs;
+    a.us = W->us;
+    a.nrhs = nrhs;
+    launch_p2p(a, s);
+  }
+  launch_permute_out(W->us, P->perm, N, nrhs, u, s);
+}
+
+template <class F>
+int guarded(F&& fn) {
+  try {
+    return fn();
+  } catch (const Error& e) {
+    return fail(e.code, e.what());
+  } catch (const std::bad_alloc&) {
+    return fail(DFMM_ERR_OOM, "host allocation failed");
+  } catch (const std::exception& e) {
+    return fail(DFMM_ERR_INVALID, e.what());
+  }
+}
+
+}  // namespace
+
+// --------------------------------------------------------------- C ABI ---
+
+extern "C" {
+
+const char* dfmm_last_error(void) { return g_err.c_str(); }
+
+int dfmm_plan(const double* points, int64_t N, double K, double eps, const dfmm_options* opts, dfmm_plan_t* out) {
+  return guarded([&]() -> int {
+    if (!out) return fail(DFMM_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!points) return fail(DFMM_ERR_INVALID, "points is NULL");
+    if (N < 1 || N > (int64_t)INT32_MAX / 2) return fail(DFMM_ERR_INVALID, "N must be in [1, 2^30]");
+    if (!(K > 0) || K > 4096) return fail(DFMM_ERR_UNSUPPORTED, "K must be in (0, 4096]");
+    if (!(eps >= 1e-8 && eps <= 1e-2)) return fail(DFMM_ERR_UNSUPPORTED, "eps must be in [1e-8, 1e-2]");
+    std::unique_ptr<dfmm_plan_s> P(new dfmm_plan_s());
+    DFMM_CUDA(cudaGetDevice(&P->device));
+    P->N = N;
+    P->K = K;
+    P->W = std::pow(2.0, std::max(0.0, std::ceil(std::log2(K))));
+    P->eps = eps;
+    dfmm_options o{};
+    if (opts) o = *opts;
+    if (o.leaf_max <= 0) o.leaf_max = 64;
+    if (o.sample_box <= 0) o.sample_box = 1024;
+    if (o.sample_far <= 0) o.sample_far = 4096;
+    if (o.sketch_rows <= 0) o.sketch_rows = 400;
+    if (!(o.eps_op_factor > 0)) o.eps_op_factor = 0.3;
+    P->opt = o;
+    P->eps_op = eps * o.eps_op_factor;
+    P->stats.N = N;
+    P->stats.K = K;
+    P->stats.W = P->W;
+    P->stats.eps = eps;
+    P->stats.eps_op = P->eps_op;
+    cudaStream_t s;
+    DFMM_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    struct SG { cudaStream_t s; ~SG() { cudaStreamDestroy(s); } } sg{s};
+    build_plan(P.get(), points, s);
+    DFMM_CUDA(cudaStreamSynchronize(s));
+    *out = P.release();
+    return DFMM_OK;
+  });
+}
+
+int dfmm_apply(dfmm_plan_t plan, const void* f, void* u, int nrhs, cudaStream_t stream) {
+  return guarded([&]() -> int {
+    if (!plan || !f || !u) return fail(DFMM_ERR_INVALID, "null argument");
+    if (nrhs < 1 || nrhs > 64) return fail(DFMM_ERR_INVALID, "nrhs must be in [1, 64]");
+    if (f == u) return fail(DFMM_ERR_INVALID, "f and u must not alias");
+    run_apply(plan, (const float2*)f, (float2*)u, nrhs, stream);
+    return DFMM_OK;
+  });
+}
+
+int dfmm_apply_host(dfmm_plan_t plan, const void* f_host, void* u_host, int nrhs, cudaStream_t stream) {
+  return guarded([&]() -> int {
+    if (!plan || !f_host || !u_host) return fail(DFMM_ERR_INVALID, "null argument");
+    if (nrhs < 1 || nrhs > 64) return fail(DFMM_ERR_INVALID, "nrhs must be in [1, 64]");
+    Workspace* W = get_workspace(plan, stream, nrhs);
+    size_t bytes = (size_t)plan->N * nrhs * sizeof(float2);
+    if (!W->f_dev) {
+      W->f_dev = W->ar.alloc<float2>(plan->N * W->nrhs);
+      W->u_dev = W->ar.alloc<float2>(plan->N * W->nrhs);
+    }
+    DFMM_CUDA(cudaMemcpyAsync(W->f_dev, f_host, bytes, cudaMemcpyHostToDevice, stream));
+    run_apply(plan, W->f_dev, W->u_dev, nrhs, stream);
+    DFMM_CUDA(cudaMemcpyAsync(u_host, W->u_dev, bytes, cudaMemcpyDeviceToHost, stream));
+    DFMM_CUDA(cudaStreamSynchronize(stream));
+    return DFMM_OK;
+  });
+}
+
+int dfmm_sync_status(dfmm_plan_t plan, cudaStream_t stream) {
+  return guarded([&]() -> int {
+    if (!plan) return fail(DFMM_ERR_INVALID, "null plan");
+    DFMM_CUDA(cudaStreamSynchronize(stream));
+    std::lock_guard<std::mutex> g(plan->ws_mu);
+    auto it = plan->ws.find(stream);
+    if (it == plan->ws.end()) return DFMM_OK;
+    unsigned st = 0;
+    DFMM_CUDA(cudaMemcpy(&st, it->second->status, 4, cudaMemcpyDeviceToHost));
+    if (st & kStatusTimeout) return fail(DFMM_ERR_TIMEOUT, "a device wait gave up");
+    if (st) return fail(DFMM_ERR_DEVICE, "a device-side check failed");
+    return DFMM_OK;
+  });
+}
+
+int dfmm_destroy(dfmm_plan_t plan) {
+  return guarded([&]() -> int {
+    if (!plan) return DFMM_OK;
+    cudaDeviceSynchronize();
+    delete plan;
+    return DFMM_OK;
+  });
+}
+
+int dfmm_plan_stats(dfmm_plan_t plan, dfmm_stats* out) {
+  if (!plan || !out) return fail(DFMM_ERR_INVALID, "null argument");
+  *out = plan->stats;
+  return DFMM_OK;
+}
+
+int64_t dfmm_apply_workspace_bytes(dfmm_plan_t plan, int nrhs) {
+  if (!plan || nrhs < 1) return -1;
+  int64_t b = 2 * plan->N * nrhs * 8;
+  for (int l = 0; l < plan->nl; ++l) {
+    if (l >= plan->l_lf0) b += 2 * plan->lf[l].nbox * nrhs * plan->lf[l].R * 8 + plan->lf[l].n_p2m * 2 * plan->lf[l].R * nrhs * 8;
+    else if (plan->l_top >= 0 && l >= plan->l_top)
+      b += ((int64_t)plan->hf[l].out_keys.size() + (int64_t)plan->hf[l].in_keys.size()) * nrhs * plan->hf[l].R * 8;
+  }
+  return b;
+}
+
+int dfmm_export(dfmm_plan_t plan, int what, void* buffer, int64_t* count) {
+  return guarded([&]() -> int {
+    if (!plan || !count) return fail(DFMM_ERR_INVALID, "null argument");
+    std::vector<int64_t> v;
+    const auto& LV = plan->tree.levels;
+    switch (what) {
+      case 0:
+        for (auto p : plan->h_perm) v.push_back(p);
+        break;
+      case 1:
+        for (auto k : plan->h_keys) v.push_back((int64_t)k);
+        break;
+      case 2:
+        for (auto& L : LV)
+          for (int64_t b = 0; b < L.n; ++b) {
+            v.push_back(L.l); v.push_back((int64_t)L.h_prefix[b]); v.push_back(L.h_first[b]);
+            v.push_back(L.h_count[b]); v.push_back(L.h_leaf[b]);
+          }
+        break;
+      case 3:
+        for (auto& H : plan->hf)
+          for (int64_t q = 0; q < H.pairs.n; ++q) {
+            v.push_back(H.l); v.push_back(H.pairs.tgt[q]); v.push_back(H.pairs.src[q]);
+            v.push_back(H.pairs.din[q]); v.push_back(H.pairs.dout[q]);
+          }
+        break;
+      case 4:
+      case 5:
+        for (auto& H : plan->hf)
+          for (int32_t k : (what == 4 ? H.out_keys : H.in_keys)) {
+            v.push_back(H.l); v.push_back(k / H.nd); v.push_back(k % H.nd);
+          }
+        break;
+      case 6:
+        for (size_t l = 0; l < plan->vlist.size(); ++l)
+          for (int64_t q = 0; q < plan->vlist[l].n; ++q) {
+            v.push_back((int64_t)l); v.push_back(plan->vlist[l].tgt[q]); v.push_back(plan->vlist[l].src[q]);
+          }
+        break;
+      case 7:
+        for (auto x : plan->U) v.push_back(x);
+        break;
+      case 8:
+        for (auto x : plan->Wl) v.push_back(x);
+        break;
+      case 9:
+        for (auto x : plan->X) v.push_back(x);
+        break;
+      case 10:
+        for (auto& r : plan->rep_ranks) { v.push_back(r[0]); v.push_back(r[1]); v.push_back(r[2]); }
+        break;
+      default:
+        return fail(DFMM_ERR_INVALID, "unknown export id");
+    }
+    int64_t n = (int64_t)v.size();
+    if (buffer) {
+      if (*count < n) return fail(DFMM_ERR_INVALID, "export buffer too small");
+      std::memcpy(buffer, v.data(), n * sizeof(int64_t));
+    }
+    *count = n;
+    return DFMM_OK;
+  });
+}
+
+int dfmm_representation(double w, int cell, double w_top, double eps_op, int sample_box, int sample_far,
+                        int sketch_rows, int* r_out, double* b2, double* a2, int cap) {
+  return guarded([&]() -> int {
+    if (!r_out) return fail(DFMM_ERR_INVALID, "r_out is NULL");
+    if (!(w > 0) || !(w_top >= 1) || !(eps_op > 0)) return fail(DFMM_ERR_INVALID, "bad representation arguments");
+    if ((cell < 0) != (w < 1)) return fail(DFMM_ERR_INVALID, "cell must be -1 exactly for w < 1");
+    if (cell >= 0 && cell >= 6 * n_cells(w) * n_cells(w)) return fail(DFMM_ERR_INVALID, "cell out of range");
+    SkelParams sp;
+    sp.eps_op = eps_op;
+    sp.S_Y = sample_box > 0 ? sample_box : 1024;
+    sp.S_X = sample_far > 0 ? sample_far : 4096;
+    sp.sketch = sketch_rows > 0 ? sketch_rows : 400;
+    Rep r = build_rep(w, cell, w_top, sp);
+    *r_out = r.r;
+    if (b2 || a2) {
+      if (2 * r.r > cap) return fail(DFMM_ERR_INVALID, "buffer capacity below 2r");
+      if (b2) std::memcpy(b2, r.b2.data(), r.b2.size() * 8);
+      if (a2) std::memcpy(a2, r.a2.data(), r.a2.size() * 8);
+    }
+    return DFMM_OK;
+  });
+}
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+"""Thin Python binding of the dfmm C ABI (include/dfmm.h).
+
+Argument marshalling only: every step of the matvec runs in the CUDA library
+libdfmm.so.  Device buffers are torch tensors (torch is used for device
+memory and streams).  If the library is missing this module raises at import
+of the first call; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdfmm.so")
+
+OK, ERR_INVALID, ERR_DOMAIN, ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED, ERR_TIMEOUT, ERR_DEVICE = 0, -1, -2, -3, -4, -5, -6, -7
+
+EXPORT = {"perm": 0, "keys": 1, "boxes": 2, "hf_pairs": 3, "slots_out": 4, "slots_in": 5, "v_pairs": 6,
+          "u_pairs": 7, "w_pairs": 8, "x_pairs": 9, "ranks": 10}
+EXPORT_COLS = {0: 1, 1: 1, 2: 5, 3: 5, 4: 3, 5: 3, 6: 3, 7: 4, 8: 4, 9: 4, 10: 3}
+
+
+class DfmmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"dfmm error {code}: {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("leaf_max", ctypes.c_int32), ("sample_box", ctypes.c_int32), ("sample_far", ctypes.c_int32),
+                ("sketch_rows", ctypes.c_int32), ("eps_op_factor", ctypes.c_double), ("m2l_mode", ctypes.c_int32),
+                ("host_threads", ctypes.c_int32), ("cache_dir", ctypes.c_char_p)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int64), ("K", ctypes.c_double), ("W", ctypes.c_double), ("eps", ctypes.c_double),
+                ("eps_op", ctypes.c_double), ("n_levels", ctypes.c_int32), ("level_hf_top", ctypes.c_int32),
+                ("level_w1", ctypes.c_int32), ("boxes", ctypes.c_int64 * 32), ("leaves", ctypes.c_int64 * 32),
+                ("hf_pairs", ctypes.c_int64 * 32), ("hf_offsets", ctypes.c_int64 * 32),
+                ("slots_out", ctypes.c_int64 * 32), ("slots_in", ctypes.c_int64 * 32),
+                ("rank", ctypes.c_int32 * 32), ("v_pairs", ctypes.c_int64), ("u_pairs", ctypes.c_int64),
+                ("w_pairs", ctypes.c_int64), ("x_pairs", ctypes.c_int64), ("p2p_interactions", ctypes.c_int64),
+                ("plan_bytes", ctypes.c_int64), ("plan_seconds", ctypes.c_double), ("m2l_flops", ctypes.c_double),
+                ("other_translation_flops", ctypes.c_double)]
+
+    def to_dict(self) -> dict:
+        n = self.n_levels
+        d = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            d[name] = list(v)[:n] if hasattr(v, "__len__") else v
+        return d
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libdfmm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1311_4257_gb300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+        L.dfmm_plan.argtypes = [vp, i64, dbl, dbl, ctypes.POINTER(Options), ctypes.POINTER(vp)]
+        L.dfmm_apply.argtypes = [vp, vp, vp, i32, vp]
+        L.dfmm_apply_host.argtypes = [vp, vp, vp, i32, vp]
+        L.dfmm_sync_status.argtypes = [vp, vp]
+        L.dfmm_destroy.argtypes = [vp]
+        L.dfmm_plan_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        L.dfmm_apply_workspace_bytes.argtypes = [vp, i32]
+        L.dfmm_apply_workspace_bytes.restype = i64
+        L.dfmm_export.argtypes = [vp, i32, vp, ctypes.POINTER(i64)]
+        L.dfmm_representation.argtypes = [dbl, i32, dbl, dbl, i32, i32, i32, ctypes.POINTER(i32), vp, vp, i32]
+        L.dfmm_last_error.restype = ctypes.c_char_p
+        for f in ("dfmm_plan", "dfmm_apply", "dfmm_apply_host", "dfmm_sync_status", "dfmm_destroy",
+                  "dfmm_plan_stats", "dfmm_export", "dfmm_representation"):
+            getattr(L, f).restype = i32
+        _lib = L
+    return _lib
+
+
+def _check(code: int):
+    if code != OK:
+        raise DfmmError(code, lib().dfmm_last_error().decode())
+
+
+def representation(w: float, cell: int, w_top: float, eps_op: float, sample_box: int = 0, sample_far: int = 0,
+                   sketch_rows: int = 0):
+    """Host-only: (rank, b2 [2r,3], a2 [2r,3]) of one representation type."""
+    r = ctypes.c_int(0)
+    cap = 1024
+    b2 = np.zeros((cap, 3))
+    a2 = np.zeros((cap, 3))
+    _check(lib().dfmm_representation(w, cell, w_top, eps_op, sample_box, sample_far, sketch_rows,
+                                      ctypes.byref(r), b2.ctypes.data, a2.ctypes.data, cap))
+    n = 2 * r.value
+    return r.value, b2[:n].copy(), a2[:n].copy()
+
+
+def _stream_ptr(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+class Plan:
+    """A resident plan: dfmm_plan(points, N, K, eps) on the current device."""
+
+    def __init__(self, points, K: float, eps: float, leaf_max: int = 0, sample_box: int = 0, sample_far: int = 0,
+                 sketch_rows: int = 0, eps_op_factor: float = 0.0, host_threads: int = 0,
+                 cache_dir: str | None = None):
+        import torch
+        if not (isinstance(points, torch.Tensor) and points.is_cuda):
+            points = torch.as_tensor(np.ascontiguousarray(points, dtype=np.float64), device="cuda")
+        points = points.to(torch.float64).contiguous()
+        if points.ndim != 2 or points.shape[1] != 3:
+            raise ValueError("points must be [N, 3]")
+        self.N = int(points.shape[0])
+        self.K = float(K)
+        self.eps = float(eps)
+        o = Options(leaf_max, sample_box, sample_far, sketch_rows, eps_op_factor, 0, host_threads,
+                    cache_dir.encode() if cache_dir else None)
+        h = ctypes.c_void_p()
+        _check(lib().dfmm_plan(points.data_ptr(), self.N, self.K, self.eps, ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+
+    def apply(self, f, u=None, stream=None):
+        """u = G f.  f: cuda complex64 [nrhs, N] (or [N]); returns u (same shape)."""
+        import torch
+        squeeze = f.ndim == 1
+        f2 = f.reshape(1, -1) if squeeze else f
+        if f2.dtype != torch.complex64 or not f2.is_cuda:
+            raise TypeError("f must be a cuda complex64 tensor")
+        f2 = f2.contiguous()
+        nrhs = int(f2.shape[0])
+        if f2.shape[1] != self.N:
+            raise ValueError("f has the wrong number of points")
+        if u is None:
+            u = torch.empty_like(f2)
+        _check(lib().dfmm_apply(self._h, f2.data_ptr(), u.data_ptr(), nrhs, _stream_ptr(stream)))
+        return u.reshape(-1) if squeeze else u
+
+    def apply_host(self, f: np.ndarray, stream=None) -> np.ndarray:
+        """Host-buffer matvec: f numpy complex64 [nrhs, N] -> u numpy complex64."""
+        f2 = np.ascontiguousarray(np.atleast_2d(f), dtype=np.complex64)
+        u = np.empty_like(f2)
+        _check(lib().dfmm_apply_host(self._h, f2.ctypes.data, u.ctypes.data, int(f2.shape[0]),
+                                     _stream_ptr(stream)))
+        return u
+
+    def sync_status(self, stream=None) -> int:
+        return lib().dfmm_sync_status(self._h, _stream_ptr(stream))
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().dfmm_plan_stats(self._h, ctypes.byref(s)))
+        return s.to_dict()
+
+    def workspace_bytes(self, nrhs: int) -> int:
+        return int(lib().dfmm_apply_workspace_bytes(self._h, nrhs))
+
+    def export(self, what) -> np.ndarray:
+        wid = EXPORT[what] if isinstance(what, str) else int(what)
+        n = ctypes.c_int64(0)
+        _check(lib().dfmm_export(self._h, wid, None, ctypes.byref(n)))
+        buf = np.zeros(max(1, n.value), dtype=np.int64)
+        _check(lib().dfmm_export(self._h, wid, buf.ctypes.data, ctypes.byref(n)))
+        return buf[:n.value].reshape(-1, EXPORT_COLS[wid])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dfmm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
