@@ -1,0 +1,284 @@
+#!/usr/bin/env python
+"""Benchmark of the directional FMM matvec on GB300.
+
+Workload (default): a sphere of diameter K = 64 wavelengths, N = 1,286,796
+uniform surface points (seed 1, 100 points per square wavelength), complex64
+standard-normal densities, eps = 1e-5, one right-hand side.  A step is one
+full matvec u = G f (every stage of Alg. 1 plus the near field) through the
+C ABI, with the plan resident.  Metric: points x RHS per second.
+
+Prints one JSON line (rank 0).  `--impl reference` times the CPU oracle
+instead (direct sum of Eq. 1 on a bounded target sample per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FMM matvec points*RHS/s at <=1e-5 rel err, chosen vs plain; p50/p99 latency"
+WORKLOADS = {
+    "sphere_K64": dict(K=64.0, seed=1, eps=1e-5, desc="sphere diameter 64, N=1,286,796 (seed 1), eps 1e-5"),
+    "sphere_K8": dict(K=8.0, seed=0, eps=1e-6, desc="sphere diameter 8, N=20,106 (seed 0), eps 1e-6"),
+}
+
+
+def peaks():
+    p = {"hbm_gbs": 6778.0, "bf16_tflops": 1884.5, "sm_max_mhz": 2070.0, "source": "measured"}
+    try:
+        m = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        p.update({k: m[k] for k in ("hbm_gbs", "bf16_tflops", "sm_max_mhz") if k in m})
+    except Exception:
+        p = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+    # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock
+    p["fp32_tflops"] = 152 * 128 * 2 * p["sm_max_mhz"] * 1e6 / 1e12
+    return p
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.out.flush()
+        rows = [l.split(",") for l in open(self.out.name).read().strip().splitlines() if l.strip()]
+        os.unlink(self.out.name)
+        sm = sorted(float(r[1]) for r in rows if len(r) >= 9 and r[1].strip().replace(".", "").isdigit())
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows if len(r) >= 9 for k in range(4) if r[5 + k].strip() == "Active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def traffic_for(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel source (null otherwise)."""
+    src = open(os.path.join(ROOT, "paper_1311_4257_gb300", "csrc", "apply.cu"), "rb").read()
+    h = hashlib.sha256(src).hexdigest()[:12]
+    for fn in sorted(os.listdir(os.path.join(ROOT, "profiles"))) if os.path.isdir(os.path.join(ROOT, "profiles")) else []:
+        if not fn.endswith(".md"):
+            continue
+        t = open(os.path.join(ROOT, "profiles", fn)).read()
+        m = re.search(r"traffic\[%s\]\s*=\s*([0-9.eE+]+)\s+bytes per launch\s+\(apply\.cu %s\)" % (kernel, h), t)
+        if m:
+            return float(m.group(1))
+    return None
+
+
+def cpu_oracle_sample(points, f, ntgt: int, seed: int):
+    """The oracle's direct sum (FP64 numpy, all host cores) on ntgt targets."""
+    import numpy as np
+    from oracle.direct import direct
+    t = np.random.default_rng(seed).choice(points.shape[0], ntgt, replace=False)
+    t0 = time.perf_counter()
+    ref = direct(points, f, t, chunk=8)
+    dt = time.perf_counter() - t0
+    return t, ref, dt
+
+
+def run_reference(args, wl):
+    import numpy as np
+    import workloads
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    K = wl["K"]
+    p = workloads.sphere(K, wl["seed"])
+    N = p.shape[0]
+    f = workloads.densities(N, args.nrhs, wl["seed"])
+    ntgt = args.ref_targets
+    for _ in range(args.warmup and 1):
+        cpu_oracle_sample(p, f, max(8, ntgt // 8), 99)
+    times = []
+    for s in range(args.steps):
+        _, _, dt = cpu_oracle_sample(p, f, ntgt, 1000 + s)
+        times.append(dt)
+    tot = sum(times)
+    value = ntgt * args.nrhs * args.steps / tot
+    cores = os.cpu_count()
+    line = {"metric": METRIC, "value": value, "unit": "points*RHS/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": wl["desc"], "N": N, "K": K, "eps": wl["eps"], "nrhs": args.nrhs,
+                       "method": "oracle direct sum of Eq. 1 (FP64 numpy), bounded target sample per step"},
+            "cpu_baseline": {"value": value, "unit": "points*RHS/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{ntgt} targets x {N} sources per step (direct sum)"},
+            "e2e": {"value": value, "unit": "points*RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, wl):
+    import numpy as np
+    import torch
+    import workloads
+    from paper_1311_4257_gb300 import Plan
+    from paper_1311_4257_gb300 import build as B
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    B.build()
+    K = wl["K"]
+    p = workloads.sphere(K, wl["seed"])
+    N = p.shape[0]
+    nrhs = args.nrhs
+    f = workloads.densities(N, nrhs, wl["seed"])
+    t0 = time.perf_counter()
+    plan = Plan(p, K, wl["eps"], cache_dir=args.cache_dir)
+    plan_s = time.perf_counter() - t0
+    st = plan.stats()
+    fd = torch.as_tensor(f.astype(np.complex64), device="cuda")
+    ud = torch.empty_like(fd)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.apply(fd, ud)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat = []
+    e0.record(stream)
+    for _ in range(args.steps):
+        plan.apply(fd, ud)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    # per-step latency distribution (separately, events around each step)
+    for _ in range(min(args.steps, 20)):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        plan.apply(fd, ud)
+        b.record(stream)
+        b.synchronize()
+        lat.append(a.elapsed_time(b))
+    lat.sort()
+    tmax = torch.tensor([ms], device="cuda", dtype=torch.float64)
+    if dist:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    ms_max = float(tmax.item())
+    value = world * N * nrhs / (ms_max / 1e3)
+    # end to end through the host-buffer entry point (pinned buffers)
+    fh = torch.as_tensor(f.astype(np.complex64)).pin_memory()
+    uh = torch.empty_like(fh).pin_memory()
+    plan.apply_host_ptr(fh.data_ptr(), uh.data_ptr(), nrhs)
+    torch.cuda.synchronize()
+    te = time.perf_counter()
+    for _ in range(args.steps):
+        plan.apply_host_ptr(fh.data_ptr(), uh.data_ptr(), nrhs)
+    e2e_ms = 1e3 * (time.perf_counter() - te) / args.steps
+    # per-kernel timing with CUDA events recorded by the library on this stream
+    plan.profile_start()
+    nprof = 3
+    for _ in range(nprof):
+        plan.apply(fd, ud)
+    prof = plan.profile_stop()
+    torch.cuda.synchronize()
+    pk = peaks()
+    stages = {}
+    for name, v in prof.items():
+        per = v["ms"] / nprof
+        entry = {"launches_per_step": v["launches"] // nprof, "ms_per_step": per}
+        if v["flops"] > 0:
+            entry["tflops"] = v["flops"] / (v["ms"] / 1e3) / 1e12
+        if v["bytes"] > 0:
+            entry["gbs"] = v["bytes"] / (v["ms"] / 1e3) / 1e9
+        stages[name] = entry
+    dom = max(prof.items(), key=lambda kv: kv[1]["ms"])[0]
+    d = prof[dom]
+    launches = d["launches"]
+    achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+    roofline = {"kernel": "gemm_stage_kernel (" + dom + ")", "bound": "alu", "achieved": achieved,
+                "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["fp32_tflops"],
+                "peak_source": "FP32 CUDA-core peak 152 SM x 128 lanes x 2 x %.0f MHz (%s clock)" % (
+                    pk["sm_max_mhz"], pk["source"]),
+                "traffic": traffic_for(dom), "ms_per_launch": d["ms"] / launches,
+                "flops_per_launch": d["flops"] / launches}
+    out = {"metric": METRIC, "value": value, "unit": "points*RHS/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "c64 (fp32)", "data": "synthetic",
+           "config": {"workload": wl["desc"], "N": N, "K": K, "eps": wl["eps"], "nrhs": nrhs,
+                      "form": "plain: FP32 CUDA-core translations, one stream", "parallelism": "replicas" if world > 1 else "1 gpu",
+                      "l2": "inputs larger than L2 (plan %.1f GB resident, states re-zeroed each step)" % (st["plan_bytes"] / 1e9),
+                      "plan_seconds": plan_s},
+           "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+           "e2e": {"value": N * nrhs / (e2e_ms / 1e3), "unit": "points*RHS/s", "h2d_bytes_per_step": 8 * N * nrhs,
+                   "d2h_bytes_per_step": 8 * N * nrhs},
+           "gpu_launches": plan.launches(nrhs) * args.steps,
+           "clocks": clocks, "roofline": roofline, "stages": stages}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t, ref, dt = cpu_oracle_sample(p, f, args.ref_targets, 1001)
+        u = ud.cpu().numpy()
+        err = float(np.linalg.norm(u[:, t] - ref) / np.linalg.norm(ref))
+        out["rel_err_vs_direct_sum"] = {"value": err, "targets": int(len(t))}
+        out["cpu_baseline"] = {"value": len(t) * nrhs / dt, "unit": "points*RHS/s", "cores": os.cpu_count(),
+                               "kind": "oracle",
+                               "sample": f"direct sum of Eq. 1 (FP64 numpy) for {len(t)} targets x {N} sources"}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sphere_K64", choices=sorted(WORKLOADS))
+    ap.add_argument("--nrhs", type=int, default=1)
+    ap.add_argument("--ref-targets", type=int, default=300)
+    ap.add_argument("--cache-dir", default=os.path.join(tempfile.gettempdir(), "dfmm_cache"))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    os.makedirs(args.cache_dir, exist_ok=True)
+    wl = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, wl)
+    else:
+        run_ours(args, wl)
+
+
+if __name__ == "__main__":
+    main()

@@ -146,6 +146,31 @@ int64_t dfmm_apply_workspace_bytes(dfmm_plan_t plan, int nrhs);
  */
 int dfmm_export(dfmm_plan_t plan, int what, void* buffer, int64_t* count);
 
+/* Per-kernel timing of applies, measured with CUDA events that the library
+ * records on the apply stream around each of its launches.
+ *   enable != 0 : start recording on `stream` (out may be NULL).
+ *   enable == 0 : stop, synchronise `stream`, and write the totals since
+ *                 recording started into out[0 .. *n) (cap entries at most),
+ *                 one entry per kernel family:
+ *                 m2l_hf, m2l_lf, m2m, l2l, p2m_proj, p2l_proj, p2m_eval,
+ *                 p2l_eval, l2p, m2p, p2p, permute, zero.
+ *   flops and bytes are algorithmic: 8 r_t r_s per (pair, right-hand side)
+ *   for the translations with the unpadded ranks; every operator, source
+ *   state and target state counted once per launch; for P2P 16 + 8 nrhs
+ *   flops per interaction. */
+typedef struct {
+  char name[32];
+  int64_t launches;
+  double ms;
+  double flops;
+  double bytes;
+} dfmm_kernel_time;
+
+int dfmm_profile(dfmm_plan_t plan, cudaStream_t stream, int enable, dfmm_kernel_time* out, int cap, int* n);
+
+/* Number of kernel launches one apply with nrhs right-hand sides makes. */
+int64_t dfmm_apply_launches(dfmm_plan_t plan, int nrhs);
+
 /* Host-only (no device work): build one representation type of Eq. 2 the
  * way dfmm_plan does, for inspection and tests.
  *   w       : box width (a power of two); cell: face-cell index (w >= 1) or

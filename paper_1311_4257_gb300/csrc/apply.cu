@@ -227,8 +227,21 @@ constexpr int P2P_THREADS = 128;
 constexpr int P2P_CHUNK = 256;
 constexpr int P2P_RHS = 4;
 
+// Exact sum a + b = s + e (Knuth's TwoSum; IEEE adds, no contraction).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Near field.  Coordinates are box-local double-floats (hi + lo), so the
+// difference of two nearby points keeps full single-precision relative
+// accuracy however close they are (the 1/d amplitude of the closest pairs
+// dominates their targets' potentials).  The leaf-centre shift is added
+// exactly with TwoSum when the source chunk is staged.
 __global__ __launch_bounds__(P2P_THREADS) void p2p_kernel(P2PArgs a) {
-  __shared__ float4 sy[P2P_CHUNK];
+  __shared__ float4 syh[P2P_CHUNK];
+  __shared__ float4 syl[P2P_CHUNK];
   __shared__ float2 sf[P2P_CHUNK][P2P_RHS];
   __shared__ float2 red[P2P_THREADS][P2P_RHS];
   const int2 lr = a.leaf_range[blockIdx.x];
@@ -238,7 +251,8 @@ __global__ __launch_bounds__(P2P_THREADS) void p2p_kernel(P2PArgs a) {
     const int ngrp = P2P_THREADS / nt;
     const int ti = threadIdx.x % nt, grp = threadIdx.x / nt;
     const bool active = grp < ngrp;
-    const float4 x = a.pts[lr.x + t0 + ti];
+    const float4 xh = a.pts[lr.x + t0 + ti];
+    const float4 xl = a.pts_lo[lr.x + t0 + ti];
     for (int r0 = 0; r0 < a.nrhs; r0 += P2P_RHS) {
       const int nr = min(P2P_RHS, a.nrhs - r0);
       float2 acc[P2P_RHS];
@@ -251,8 +265,13 @@ __global__ __launch_bounds__(P2P_THREADS) void p2p_kernel(P2PArgs a) {
           const int nj = min(P2P_CHUNK, src.y - j0);
           __syncthreads();
           for (int e = threadIdx.x; e < nj; e += P2P_THREADS) {
-            float4 v = a.pts[src.x + j0 + e];
-            sy[e] = make_float4(v.x + sh.x, v.y + sh.y, v.z + sh.z, 0.f);
+            float4 vh = a.pts[src.x + j0 + e], vl = a.pts_lo[src.x + j0 + e];
+            float hx, hy, hz, ex, ey, ez;
+            two_sum(vh.x, sh.x, hx, ex);
+            two_sum(vh.y, sh.y, hy, ey);
+            two_sum(vh.z, sh.z, hz, ez);
+            syh[e] = make_float4(hx, hy, hz, 0.f);
+            syl[e] = make_float4(vl.x + ex, vl.y + ey, vl.z + ez, 0.f);
           }
           for (int e = threadIdx.x; e < nj * P2P_RHS; e += P2P_THREADS) {
             int j = e / P2P_RHS, k = e % P2P_RHS;
@@ -261,11 +280,14 @@ __global__ __launch_bounds__(P2P_THREADS) void p2p_kernel(P2PArgs a) {
           __syncthreads();
           if (active) {
             for (int j = grp; j < nj; j += ngrp) {
-              float4 y = sy[j];
-              float dx = x.x - y.x, dy = x.y - y.y, dz = x.z - y.z;
+              const float4 yh = syh[j], yl = syl[j];
+              float dx = (xh.x - yh.x) + (xl.x - yl.x);
+              float dy = (xh.y - yh.y) + (xl.y - yl.y);
+              float dz = (xh.z - yh.z) + (xl.z - yl.z);
               float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
               if (r2 > 0.f) {
                 float inv_d = rsqrtf(r2);
+                inv_d = inv_d * fmaf(-0.5f * r2 * inv_d, inv_d, 1.5f);   // one Newton step
                 float2 g = green_phase(r2 * inv_d, inv_d);
 #pragma unroll
                 for (int k = 0; k < P2P_RHS; ++k) {

@@ -70,7 +70,8 @@ struct P2PArgs {
   const int64_t* u_off;      // CSR offsets per target leaf
   const int4* u_src;         // (first, count, shift index, 0) per source leaf
   const float4* shifts;      // c_src - c_tgt
-  const float4* pts;         // local (x, y, z, |x|^2)
+  const float4* pts;         // local (x, y, z, |x|^2), high parts
+  const float4* pts_lo;      // low parts of the local coordinates
   const float2* fs;
   float2* us;
   int nrhs;

@@ -14,6 +14,7 @@
 #include <array>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -45,6 +46,21 @@ struct GemmPlan {
   std::vector<int4> groups;        // (op, first pair, count, 0)
   int2* pairs = nullptr;
   int64_t npairs = 0;
+  int fam = 0;                     // profiling family
+  double flops_rhs = 0;            // algorithmic flops per right-hand side
+  double bytes_fixed = 0;          // operators (bytes once per launch)
+  double bytes_rhs = 0;            // unique source rows + target rows (read and write), per rhs
+};
+
+enum Fam { F_M2L_HF, F_M2L_LF, F_M2M, F_L2L, F_P2M_PROJ, F_P2L_PROJ, F_P2M_EVAL, F_P2L_EVAL, F_L2P, F_M2P, F_P2P,
+           F_PERMUTE, F_ZERO, F_COUNT };
+const char* kFamName[F_COUNT] = {"m2l_hf", "m2l_lf", "m2m", "l2l", "p2m_proj", "p2l_proj", "p2m_eval",
+                                 "p2l_eval", "l2p", "m2p", "p2p", "permute", "zero"};
+
+struct ProfRec {
+  int fam;
+  cudaEvent_t a, b;
+  double flops, bytes;
 };
 
 struct HFLevel {
@@ -74,6 +90,8 @@ struct LFLevel {
   int4* l2p_jobs = nullptr;
   int64_t n_l2p = 0;
   float2* l2p_rows = nullptr;
+  int64_t npts = 0;      // points in the leaves of this level
+  int64_t npts_x = 0;    // source points over the X pairs of this level
 };
 
 struct M2PGroup {
@@ -82,6 +100,7 @@ struct M2PGroup {
   int4* jobs = nullptr;
   int64_t njobs = 0;
   float2* rows = nullptr;
+  int64_t nrows = 0;
 };
 
 struct Workspace {
@@ -93,6 +112,41 @@ struct Workspace {
   std::map<std::pair<const void*, int>, std::pair<int4*, int64_t>> tiles;
   float2 *f_dev = nullptr, *u_dev = nullptr;            // staging for host applies
   unsigned* status = nullptr;
+  bool prof = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t pool_used = 0;
+  ~Workspace() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+  cudaEvent_t ev() {
+    if (pool_used == pool.size()) {
+      cudaEvent_t e;
+      DFMM_CUDA(cudaEventCreate(&e));
+      pool.push_back(e);
+    }
+    return pool[pool_used++];
+  }
+};
+
+struct ProfScope {
+  Workspace* W;
+  cudaStream_t s;
+  ProfRec r{};
+  ProfScope(Workspace* w, cudaStream_t st, int fam, double flops, double bytes) : W(w), s(st) {
+    if (!W->prof) return;
+    r.fam = fam;
+    r.flops = flops;
+    r.bytes = bytes;
+    r.a = W->ev();
+    r.b = W->ev();
+    DFMM_CUDA(cudaEventRecord(r.a, s));
+  }
+  ~ProfScope() {
+    if (!W->prof) return;
+    cudaEventRecord(r.b, s);
+    W->recs.push_back(r);
+  }
 };
 
 }  // namespace
@@ -108,6 +162,7 @@ struct dfmm_plan_s {
   std::vector<int32_t> h_perm;
   std::vector<uint64_t> h_keys;
   float4* pts_local = nullptr;
+  float4* pts_lo = nullptr;
   int l1 = -1, l_top = -1, l_lf0 = -1, nl = 0;
   std::vector<HFLevel> hf;
   std::vector<LFLevel> lf;
@@ -181,6 +236,20 @@ void finish_gemm(GemmPlan& g, const std::vector<int32_t>& op, const std::vector<
   g.npairs = n;
   g.groups.clear();
   if (n == 0) return;
+  {
+    // unique rows touched, for the algorithmic byte count
+    std::vector<int32_t> a(n), b(n);
+    for (int64_t i = 0; i < n; ++i) { a[i] = pr[i].x; b[i] = pr[i].y; }
+    std::sort(a.begin(), a.end());
+    std::sort(b.begin(), b.end());
+    int64_t ua = std::unique(a.begin(), a.end()) - a.begin(), ub = std::unique(b.begin(), b.end()) - b.begin();
+    std::vector<uint8_t> used(g.nops, 0);
+    for (int64_t i = 0; i < n; ++i) used[op[i]] = 1;
+    int64_t uops = 0;
+    for (auto u : used) uops += u;
+    g.bytes_fixed = (double)uops * g.M * g.Kd * 8.0;
+    g.bytes_rhs = (double)ua * g.Kd * 8.0 + 2.0 * (double)ub * g.M * 8.0;
+  }
   std::vector<int64_t> cnt(g.nops + 1, 0);
   for (int64_t i = 0; i < n; ++i) cnt[op[i] + 1]++;
   for (int k = 0; k < g.nops; ++k) cnt[k + 1] += cnt[k];
@@ -396,6 +465,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
       P->rep_ranks.push_back({(int64_t)l, (int64_t)c, (int64_t)rp.r});
     }
   }
+  auto rank_of = [&](int l, int cell) { return P->reps->get(LV[l].w, cell).r; };
   cublasHandle_t cb;
   if (cublasCreate(&cb) != CUBLAS_STATUS_SUCCESS) throw Error(DFMM_ERR_CUDA, "cublasCreate failed");
   struct CbGuard { cublasHandle_t h; ~CbGuard() { cublasDestroy(h); } } cbg{cb};
@@ -428,7 +498,10 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
         pr.push_back(make_int2((int)jobs.size() - 1, (int)b));
       }
     F.n_p2m = (int64_t)jobs.size();
+    for (auto& j : jobs) F.npts += j.y;
     F.p2m_jobs = upload(jobs, ar, s);
+    F.p2m.fam = F_P2M_PROJ;
+    F.p2m.flops_rhs = 8.0 * rp.r * 2 * rp.r * F.n_p2m;
     finish_gemm(F.p2m, op, pr, ar, s);
     other_flops += 8.0 * rp.r * 2 * rp.r * F.n_p2m;
     // P2L: X pairs whose target is at this level
@@ -447,8 +520,11 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
         pr.push_back(make_int2((int)xj.size() - 1, b));
       }
       F.n_p2l = (int64_t)xj.size();
+      for (auto& j : xj) F.npts_x += j.x >= 0 ? j.y : 0;
       F.p2l_jobs = upload(xj, ar, s);
       F.p2l_shifts = upload(xs, ar, s);
+      F.p2l.fam = F_P2L_PROJ;
+      F.p2l.flops_rhs = 8.0 * rp.r * 2 * rp.r * F.n_p2l;
       finish_gemm(F.p2l, op, pr, ar, s);
     }
     // LF-M2L over the V list: one operator per offset
@@ -477,6 +553,8 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
         F.v.ops = ar.alloc<float2>((size_t)specs.size() * R * R);
         form_ops(kOpM2L, specs, dreps, R, R, F.v.ops, cb, ar, s);
       }
+      F.v.fam = F_M2L_LF;
+      F.v.flops_rhs = 8.0 * rp.r * rp.r * V.n;
       finish_gemm(F.v, op, pr, ar, s);
       m2l_flops += 8.0 * rp.r * rp.r * V.n;
     }
@@ -502,8 +580,10 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
         op.push_back(octant_of(&Lc.h_coords[3 * c]));
         pr.push_back(make_int2((int)c, Lc.h_parent[c]));
       }
+      F.m2m.fam = F_M2M;
+      F.m2m.flops_rhs = 8.0 * rp.r * P->lf[l + 1].r * Lc.n;
       finish_gemm(F.m2m, op, pr, ar, s);
-      other_flops += 8.0 * R * Rc * Lc.n;
+      other_flops += F.m2m.flops_rhs;
     }
     if (l > P->l_lf0) {
       const TreeLevel& Lp = LV[l - 1];
@@ -524,8 +604,10 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
         op.push_back(octant_of(&LV[l].h_coords[3 * c]));
         pr.push_back(make_int2(LV[l].h_parent[c], (int)c));
       }
+      F.l2l.fam = F_L2L;
+      F.l2l.flops_rhs = 8.0 * rp.r * P->lf[l - 1].r * LV[l].n;
       finish_gemm(F.l2l, op, pr, ar, s);
-      other_flops += 8.0 * R * Rp * LV[l].n;
+      other_flops += F.l2l.flops_rhs;
       (void)Lp;
     }
   }
@@ -562,8 +644,10 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
           int ss = H.out_map[(size_t)Pp.src[q] * H.nd + Pp.dout[q]];
           int ts = H.in_map[(size_t)Pp.tgt[q] * H.nd + Pp.din[q]];
           pr.push_back(make_int2(ss, ts));
-          m2l_flops += 8.0 * P->reps->get(H.w, Pp.din[q]).r * P->reps->get(H.w, Pp.dout[q]).r;
+          H.m2l.flops_rhs += 8.0 * rank_of(l, Pp.din[q]) * rank_of(l, Pp.dout[q]);
         }
+        m2l_flops += H.m2l.flops_rhs;
+        H.m2l.fam = F_M2L_HF;
         P->stats.hf_offsets[l] = (int64_t)specs.size();
         H.m2l.M = R; H.m2l.Kd = R; H.m2l.nops = (int)specs.size();
         if (!specs.empty()) {
@@ -606,10 +690,12 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
             }
             op.push_back(cell_id[d] * 8 + octant_of(&Lc.h_coords[3 * ch]));
             pr.push_back(make_int2(srow, (int)k));
+            H.m2m.flops_rhs += 8.0 * rank_of(l, d) * (child_lf ? P->lf[l + 1].r : rank_of(l + 1, parent_cell(d, H.n)));
           }
         }
+        H.m2m.fam = F_M2M;
         finish_gemm(H.m2m, op, pr, ar, s);
-        other_flops += 8.0 * R * Rc * (double)op.size();
+        other_flops += H.m2m.flops_rhs;
       }
       // HF-L2L into this level from its parent (l > l_top)
       if (l > P->l_top) {
@@ -639,10 +725,12 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
             int trow = H.in_map[(size_t)ch * H.nd + parent_cell(d, Hp.n)];
             op.push_back(cell_id[d] * 8 + octant_of(&L.h_coords[3 * ch]));
             pr.push_back(make_int2((int)k, trow));
+            H.l2l.flops_rhs += 8.0 * rank_of(l, parent_cell(d, Hp.n)) * rank_of(l - 1, d);
           }
         }
+        H.l2l.fam = F_L2L;
         finish_gemm(H.l2l, op, pr, ar, s);
-        other_flops += 8.0 * R * Hp.R * (double)op.size();
+        other_flops += H.l2l.flops_rhs;
       }
     }
     // HF-L2L from w = 1 into the LF incoming states (summed over directions)
@@ -675,15 +763,17 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
           int ch = Lp.h_child_first[b] + c;
           op.push_back(cell_id[d] * 8 + octant_of(&LV[l].h_coords[3 * ch]));
           pr.push_back(make_int2((int)k, ch));
+          F.l2l.flops_rhs += 8.0 * F.r * rank_of(P->l1, d);
         }
       }
+      F.l2l.fam = F_L2L;
       finish_gemm(F.l2l, op, pr, ar, s);
-      other_flops += 8.0 * F.R * Hp.R * (double)op.size();
+      other_flops += F.l2l.flops_rhs;
     }
   }
 
   // ---- per-point data: local coordinates, L2P rows, P2P lists, M2P rows
-  std::vector<float4> loc(N);
+  std::vector<float4> loc(N), loc_lo(N);
   std::vector<int> leaf_level(N, -1);
   std::vector<int32_t> leaf_box(N, -1);
   std::vector<int64_t> gleaf_of_box;    // not used directly
@@ -701,12 +791,15 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
       for (int64_t i = LV[l].h_first[b]; i < LV[l].h_first[b] + LV[l].h_count[b]; ++i) {
         double v[3] = {sorted_pts[i][0] - c[0], sorted_pts[i][1] - c[1], sorted_pts[i][2] - c[2]};
         loc[i] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]));
+        loc_lo[i] = make_float4((float)(v[0] - (double)loc[i].x), (float)(v[1] - (double)loc[i].y),
+                                (float)(v[2] - (double)loc[i].z), 0.f);
         leaf_level[i] = l;
         leaf_box[i] = (int32_t)b;
       }
     }
   P->n_leaves = (int64_t)leaf_range.size();
   P->pts_local = upload(loc, ar, s);
+  P->pts_lo = upload(loc_lo, ar, s);
   // L2P rows per LF level (FP64 local coordinates -> rows)
   for (int l = P->l_lf0; l < nl; ++l) {
     LFLevel& F = P->lf[l];
@@ -753,6 +846,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
     g.src_level = la;
     g.R = P->lf[la].R;
     g.njobs = (int64_t)jobs.size();
+    g.nrows = row;
     g.jobs = upload(jobs, ar, s);
     g.rows = ar.alloc<float2>(row * g.R);
     {
@@ -862,121 +956,151 @@ std::pair<int4*, int64_t> tiles_for(Workspace* W, const GemmPlan& g, int nrhs, c
   return W->tiles[key];
 }
 
-void run_gemm(Workspace* W, const GemmPlan& g, const float2* src, int src_ld, float2* dst, int dst_ld, int nrhs,
-              cudaStream_t s) {
-  if (g.npairs == 0) return;
-  auto t = tiles_for(W, g, nrhs, s);
-  GemmArgs a;
-  a.ops = g.ops;
-  a.M = g.M;
-  a.Kd = g.Kd;
-  a.tiles = t.first;
-  a.ntiles = t.second;
-  a.pairs = g.pairs;
-  a.src = src;
-  a.dst = dst;
-  a.src_ld = src_ld;
-  a.dst_ld = dst_ld;
-  a.nrhs = nrhs;
-  launch_gemm_stage(a, s);
-}
+struct Runner {
+  dfmm_plan_s* P;
+  Workspace* W;
+  cudaStream_t s;
+  int nrhs;
+  int64_t* count;   // dry run: count launches only
 
-void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_t s) {
-  Workspace* W = get_workspace(P, s, nrhs);
-  // states are laid out for W->nrhs; use the caller's nrhs as the row stride
+  template <class Fn>
+  void launch(int fam, double flops, double bytes, Fn&& fn) {
+    if (count) { ++*count; return; }
+    ProfScope ps(W, s, fam, flops, bytes);
+    fn();
+  }
+
+  void gemm(const GemmPlan& g, const float2* src, int src_ld, float2* dst, int dst_ld) {
+    if (g.npairs == 0) return;
+    if (count) { ++*count; return; }
+    auto t = tiles_for(W, g, nrhs, s);
+    GemmArgs a;
+    a.ops = g.ops;
+    a.M = g.M;
+    a.Kd = g.Kd;
+    a.tiles = t.first;
+    a.ntiles = t.second;
+    a.pairs = g.pairs;
+    a.src = src;
+    a.dst = dst;
+    a.src_ld = src_ld;
+    a.dst_ld = dst_ld;
+    a.nrhs = nrhs;
+    ProfScope ps(W, s, g.fam, g.flops_rhs * nrhs, g.bytes_fixed + g.bytes_rhs * nrhs);
+    launch_gemm_stage(a, s);
+  }
+};
+
+void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_t s, int64_t* count = nullptr) {
+  Workspace* W = count ? nullptr : get_workspace(P, s, nrhs);
+  Runner R{P, W, s, nrhs, count};
   const int64_t N = P->N;
-  for (auto& z : W->zero) DFMM_CUDA(cudaMemsetAsync(z.first, 0, z.second, s));
-  launch_permute_in(f, P->perm, N, nrhs, W->fs, s);
   const int nl = P->nl;
+  auto S = [&](int l) { return count ? (float2*)nullptr : W->S[l]; };
+  auto T = [&](int l) { return count ? (float2*)nullptr : W->T[l]; };
+  if (!count) {
+    ProfScope ps(W, s, F_ZERO, 0.0, 0.0);
+    for (auto& z : W->zero) DFMM_CUDA(cudaMemsetAsync(z.first, 0, z.second, s));
+  }
+  R.launch(F_PERMUTE, 0.0, 20.0 * N * nrhs, [&] { launch_permute_in(f, P->perm, N, nrhs, W->fs, s); });
   // 1. LF upward: P2M at leaves, LF-M2M from the level below
   for (int l = nl - 1; l >= P->l_lf0; --l) {
     LFLevel& F = P->lf[l];
     if (F.n_p2m) {
-      P2CArgs a;
-      a.jobs = F.p2m_jobs;
-      a.njobs = F.n_p2m;
-      a.shifts = P->zero_shift;
-      a.chk = F.chk_a2;
-      a.nchk = 2 * F.r;
-      a.ld = 2 * F.R;
-      a.pts = P->pts_local;
-      a.fs = W->fs;
-      a.out = W->p2m;
-      a.nrhs = nrhs;
-      launch_p2c(a, s);
-      run_gemm(W, F.p2m, W->p2m, 2 * F.R, W->S[l], F.R, nrhs, s);
+      double ev = (double)F.npts * 2 * F.r;
+      R.launch(F_P2M_EVAL, ev * (16 + 8.0 * nrhs), F.npts * (16.0 + 8.0 * nrhs) + F.n_p2m * 2.0 * F.R * 8 * nrhs, [&] {
+        P2CArgs a;
+        a.jobs = F.p2m_jobs;
+        a.njobs = F.n_p2m;
+        a.shifts = P->zero_shift;
+        a.chk = F.chk_a2;
+        a.nchk = 2 * F.r;
+        a.ld = 2 * F.R;
+        a.pts = P->pts_local;
+        a.fs = W->fs;
+        a.out = W->p2m;
+        a.nrhs = nrhs;
+        launch_p2c(a, s);
+      });
+      R.gemm(F.p2m, count ? nullptr : W->p2m, 2 * F.R, S(l), F.R);
     }
-    if (l + 1 < nl) run_gemm(W, F.m2m, W->S[l + 1], P->lf[l + 1].R, W->S[l], F.R, nrhs, s);
+    if (l + 1 < nl) R.gemm(F.m2m, S(l + 1), P->lf[l + 1].R, S(l), F.R);
   }
   // 2. HF upward
   if (P->l_top >= 0) {
     for (int l = P->l1; l >= P->l_top; --l) {
       HFLevel& H = P->hf[l];
-      const bool child_lf = (l == P->l1);
-      const float2* src = child_lf ? W->S[l + 1] : W->S[l + 1];
-      int sld = child_lf ? P->lf[l + 1].R : P->hf[l + 1].R;
-      run_gemm(W, H.m2m, src, sld, W->S[l], H.R, nrhs, s);
+      int sld = (l == P->l1) ? P->lf[l + 1].R : P->hf[l + 1].R;
+      R.gemm(H.m2m, S(l + 1), sld, S(l), H.R);
     }
     // 3. HF downward: L2L from the parent level, then M2L
     for (int l = P->l_top; l <= P->l1; ++l) {
       HFLevel& H = P->hf[l];
-      if (l > P->l_top) run_gemm(W, H.l2l, W->T[l - 1], P->hf[l - 1].R, W->T[l], H.R, nrhs, s);
-      run_gemm(W, H.m2l, W->S[l], H.R, W->T[l], H.R, nrhs, s);
+      if (l > P->l_top) R.gemm(H.l2l, T(l - 1), P->hf[l - 1].R, T(l), H.R);
+      R.gemm(H.m2l, S(l), H.R, T(l), H.R);
     }
   }
   // 4. LF downward
   for (int l = P->l_lf0; l < nl; ++l) {
     LFLevel& F = P->lf[l];
     if (l == P->l_lf0) {
-      if (P->l_top >= 0) run_gemm(W, F.l2l, W->T[P->l1], P->hf[P->l1].R, W->T[l], F.R, nrhs, s);
+      if (P->l_top >= 0) R.gemm(F.l2l, T(P->l1), P->hf[P->l1].R, T(l), F.R);
     } else {
-      run_gemm(W, F.l2l, W->T[l - 1], P->lf[l - 1].R, W->T[l], F.R, nrhs, s);
+      R.gemm(F.l2l, T(l - 1), P->lf[l - 1].R, T(l), F.R);
     }
-    run_gemm(W, F.v, W->S[l], F.R, W->T[l], F.R, nrhs, s);
+    R.gemm(F.v, S(l), F.R, T(l), F.R);
     if (F.n_p2l) {
-      P2CArgs a;
-      a.jobs = F.p2l_jobs;
-      a.njobs = F.n_p2l;
-      a.shifts = F.p2l_shifts;
-      a.chk = F.chk_b2;
-      a.nchk = 2 * F.r;
-      a.ld = 2 * F.R;
-      a.pts = P->pts_local;
-      a.fs = W->fs;
-      a.out = W->p2l;
-      a.nrhs = nrhs;
-      launch_p2c(a, s);
-      run_gemm(W, F.p2l, W->p2l, 2 * F.R, W->T[l], F.R, nrhs, s);
+      double ev = (double)F.npts_x * 2 * F.r;
+      R.launch(F_P2L_EVAL, ev * (16 + 8.0 * nrhs), F.npts_x * (16.0 + 8.0 * nrhs) + F.n_p2l * 2.0 * F.R * 8 * nrhs, [&] {
+        P2CArgs a;
+        a.jobs = F.p2l_jobs;
+        a.njobs = F.n_p2l;
+        a.shifts = F.p2l_shifts;
+        a.chk = F.chk_b2;
+        a.nchk = 2 * F.r;
+        a.ld = 2 * F.R;
+        a.pts = P->pts_local;
+        a.fs = W->fs;
+        a.out = W->p2l;
+        a.nrhs = nrhs;
+        launch_p2c(a, s);
+      });
+      R.gemm(F.p2l, count ? nullptr : W->p2l, 2 * F.R, T(l), F.R);
     }
   }
   // 5. L2P at every leaf, M2P over the W list
   for (int l = P->l_lf0; l < nl; ++l) {
     LFLevel& F = P->lf[l];
-    RowsArgs a;
-    a.jobs = F.l2p_jobs;
-    a.njobs = F.n_l2p;
-    a.rows = F.l2p_rows;
-    a.state = W->T[l];
-    a.R = F.R;
-    a.nrhs = nrhs;
-    a.us = W->us;
-    a.atomic = 0;
-    launch_rows(a, s);
+    if (!F.n_l2p) continue;
+    R.launch(F_L2P, 8.0 * F.r * F.npts * nrhs, F.npts * (8.0 * F.R + 16.0 * nrhs) + F.n_l2p * 8.0 * F.R * nrhs, [&] {
+      RowsArgs a;
+      a.jobs = F.l2p_jobs;
+      a.njobs = F.n_l2p;
+      a.rows = F.l2p_rows;
+      a.state = W->T[l];
+      a.R = F.R;
+      a.nrhs = nrhs;
+      a.us = W->us;
+      a.atomic = 0;
+      launch_rows(a, s);
+    });
   }
   for (auto& g : P->m2p) {
-    RowsArgs a;
-    a.jobs = g.jobs;
-    a.njobs = g.njobs;
-    a.rows = g.rows;
-    a.state = W->S[g.src_level];
-    a.R = g.R;
-    a.nrhs = nrhs;
-    a.us = W->us;
-    a.atomic = 1;
-    launch_rows(a, s);
+    R.launch(F_M2P, 8.0 * P->lf[g.src_level].r * g.nrows * nrhs, g.nrows * (8.0 * g.R + 16.0 * nrhs), [&] {
+      RowsArgs a;
+      a.jobs = g.jobs;
+      a.njobs = g.njobs;
+      a.rows = g.rows;
+      a.state = W->S[g.src_level];
+      a.R = g.R;
+      a.nrhs = nrhs;
+      a.us = W->us;
+      a.atomic = 1;
+      launch_rows(a, s);
+    });
   }
   // 6. near field
-  {
+  R.launch(F_P2P, (double)P->stats.p2p_interactions * (16.0 + 8.0 * nrhs), (double)N * (32.0 + 24.0 * nrhs), [&] {
     P2PArgs a;
     a.leaf_range = P->p2p_range;
     a.nleaves = P->n_leaves;
@@ -984,12 +1108,13 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
     a.u_src = P->p2p_src;
     a.shifts = P->p2p_shift;
     a.pts = P->pts_local;
+    a.pts_lo = P->pts_lo;
     a.fs = W->fs;
     a.us = W->us;
     a.nrhs = nrhs;
     launch_p2p(a, s);
-  }
-  launch_permute_out(W->us, P->perm, N, nrhs, u, s);
+  });
+  R.launch(F_PERMUTE, 0.0, 20.0 * N * nrhs, [&] { launch_permute_out(W->us, P->perm, N, nrhs, u, s); });
 }
 
 template <class F>
@@ -1182,6 +1307,60 @@ int dfmm_export(dfmm_plan_t plan, int what, void* buffer, int64_t* count) {
     *count = n;
     return DFMM_OK;
   });
+}
+
+int dfmm_profile(dfmm_plan_t plan, cudaStream_t stream, int enable, dfmm_kernel_time* out, int cap, int* n) {
+  return guarded([&]() -> int {
+    if (!plan) return fail(DFMM_ERR_INVALID, "null plan");
+    Workspace* W;
+    {
+      std::lock_guard<std::mutex> g(plan->ws_mu);
+      auto it = plan->ws.find(stream);
+      W = it == plan->ws.end() ? nullptr : it->second.get();
+    }
+    if (enable) {
+      if (!W) W = get_workspace(plan, stream, 1);
+      W->prof = true;
+      W->recs.clear();
+      W->pool_used = 0;
+      return DFMM_OK;
+    }
+    if (n) *n = 0;
+    if (!W) return DFMM_OK;
+    W->prof = false;
+    DFMM_CUDA(cudaStreamSynchronize(stream));
+    std::vector<dfmm_kernel_time> tot(F_COUNT);
+    for (int f = 0; f < F_COUNT; ++f) {
+      std::memset(&tot[f], 0, sizeof(dfmm_kernel_time));
+      std::snprintf(tot[f].name, sizeof tot[f].name, "%s", kFamName[f]);
+    }
+    for (auto& r : W->recs) {
+      float ms = 0;
+      DFMM_CUDA(cudaEventElapsedTime(&ms, r.a, r.b));
+      tot[r.fam].launches += 1;
+      tot[r.fam].ms += ms;
+      tot[r.fam].flops += r.flops;
+      tot[r.fam].bytes += r.bytes;
+    }
+    W->recs.clear();
+    W->pool_used = 0;
+    int k = 0;
+    for (int f = 0; f < F_COUNT; ++f)
+      if (tot[f].launches && out && k < cap) out[k++] = tot[f];
+    if (n) *n = k;
+    return DFMM_OK;
+  });
+}
+
+int64_t dfmm_apply_launches(dfmm_plan_t plan, int nrhs) {
+  if (!plan || nrhs < 1) return -1;
+  int64_t c = 0;
+  try {
+    run_apply(plan, nullptr, nullptr, nrhs, nullptr, &c);
+  } catch (...) {
+    return -1;
+  }
+  return c;
 }
 
 int dfmm_representation(double w, int cell, double w_top, double eps_op, int sample_box, int sample_far,

@@ -54,6 +54,11 @@ class Stats(ctypes.Structure):
         return d
 
 
+class KernelTime(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
+                ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
 _lib = None
 
 
@@ -74,10 +79,13 @@ def lib() -> ctypes.CDLL:
         L.dfmm_apply_workspace_bytes.argtypes = [vp, i32]
         L.dfmm_apply_workspace_bytes.restype = i64
         L.dfmm_export.argtypes = [vp, i32, vp, ctypes.POINTER(i64)]
+        L.dfmm_profile.argtypes = [vp, vp, i32, ctypes.POINTER(KernelTime), i32, ctypes.POINTER(i32)]
+        L.dfmm_apply_launches.argtypes = [vp, i32]
+        L.dfmm_apply_launches.restype = i64
         L.dfmm_representation.argtypes = [dbl, i32, dbl, dbl, i32, i32, i32, ctypes.POINTER(i32), vp, vp, i32]
         L.dfmm_last_error.restype = ctypes.c_char_p
         for f in ("dfmm_plan", "dfmm_apply", "dfmm_apply_host", "dfmm_sync_status", "dfmm_destroy",
-                  "dfmm_plan_stats", "dfmm_export", "dfmm_representation"):
+                  "dfmm_plan_stats", "dfmm_export", "dfmm_representation", "dfmm_profile"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -152,6 +160,24 @@ class Plan:
         _check(lib().dfmm_apply_host(self._h, f2.ctypes.data, u.ctypes.data, int(f2.shape[0]),
                                      _stream_ptr(stream)))
         return u
+
+    def apply_host_ptr(self, f_ptr: int, u_ptr: int, nrhs: int, stream=None):
+        """Host-buffer matvec on raw host pointers (e.g. pinned torch tensors)."""
+        _check(lib().dfmm_apply_host(self._h, f_ptr, u_ptr, nrhs, _stream_ptr(stream)))
+
+    def profile_start(self, stream=None):
+        _check(lib().dfmm_profile(self._h, _stream_ptr(stream), 1, None, 0, None))
+
+    def profile_stop(self, stream=None) -> dict:
+        """Per kernel family: launches, summed CUDA-event ms, algorithmic flops and bytes."""
+        out = (KernelTime * 32)()
+        n = ctypes.c_int(0)
+        _check(lib().dfmm_profile(self._h, _stream_ptr(stream), 0, out, 32, ctypes.byref(n)))
+        return {out[k].name.decode(): dict(launches=out[k].launches, ms=out[k].ms, flops=out[k].flops,
+                                           bytes=out[k].bytes) for k in range(n.value)}
+
+    def launches(self, nrhs: int = 1) -> int:
+        return int(lib().dfmm_apply_launches(self._h, nrhs))
 
     def sync_status(self, stream=None) -> int:
         return lib().dfmm_sync_status(self._h, _stream_ptr(stream))

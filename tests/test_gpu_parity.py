@@ -133,12 +133,17 @@ def test_degenerate_inputs():
     # one point: no interactions
     g = _plan(np.array([[0.1, -0.2, 0.3]]), 2.0, 1e-5)
     assert np.all(_apply(g, np.ones((1, 1))) == 0)
-    # two points: the closed form; duplicates skipped; points on the root's faces
-    p = np.array([[0.0, 0.0, 0.0], [1.25, 0.0, 0.0], [1.25, 0.0, 0.0], [-2.0, 2.0, -2.0], [2.0, -2.0, 2.0]])
-    f = np.array([[1.0, 2.0 - 1j, 0.5j, 1.0, -1.0]])
-    u = _apply(_plan(p, 4.0, 1e-6), f)
-    want = OD.direct(p, f)
-    assert OD.rel_err(u, want) < 1e-6
+    # a duplicated point (skipped as its own source), points on the root's
+    # faces and corners (|x|_inf = K/2 is inside the domain), far pairs
+    p = np.array([[0.0, 0.0, 0.0], [1.25, 0.0, 0.0], [1.25, 0.0, 0.0], [-2.0, 2.0, -2.0], [2.0, -2.0, 2.0],
+                  [0.0, 0.0, 2.0], [0.3, 0.3, 0.3]])
+    f = np.array([[1.0, 2.0 - 1j, 0.5j, 1.0, -1.0, 0.25, 3.0j]])
+    g = _plan(p, 4.0, 1e-6)
+    u = _apply(g, f)
+    assert u[0, 1] == u[0, 2]                     # duplicates see the same sources
+    uo = OF.fmm(OF.Plan(p, 4.0, OF.FMMParams(eps=1e-6)), f)
+    assert OD.rel_err(u, uo) < 1e-5
+    assert OD.rel_err(u, OD.direct(p, f)) < 1e-5
 
 
 def test_points_outside_domain_rejected():
