@@ -146,6 +146,32 @@ int64_t dfmm_apply_workspace_bytes(dfmm_plan_t plan, int nrhs);
  */
 int dfmm_export(dfmm_plan_t plan, int what, void* buffer, int64_t* count);
 
+/* The matvec of dfmm_apply without allocating device memory.
+ *
+ * The paper has no counterpart: this entry point serves callers that must not
+ * let a library call cudaMalloc or cudaFree, such as code running while a
+ * CUDA graph is captured, request paths of services that forbid allocation
+ * after start-up, or hosts whose device memory is budgeted in advance.
+ * Every per-apply buffer (sorted densities and potentials, the translation
+ * states, the staging buffers and the work tables) is laid out in one
+ * file-scope device array of dfmm_noalloc_capacity() bytes (64 MiB), which
+ * every device that loads the library holds until the process exits.
+ *   plan, f, u, nrhs, stream : as for dfmm_apply (device pointers, complex64
+ *            [nrhs][N], u overwritten).  The plan must belong to the current
+ *            device.
+ * Returns DFMM_ERR_UNSUPPORTED, with the required size in the message, when
+ * the apply needs more scratch than the array holds (roughly N * nrhs above
+ * 10^5 at the default tolerances).
+ * The first call on a device looks up the array's device address on that
+ * device; make that first call before any stream capture.  All calls share
+ * the one array and each overwrites what the previous left there: calls that
+ * overlap on the GPU (other streams, other threads) race on it and must be
+ * serialised by the caller. */
+int dfmm_apply_noalloc(dfmm_plan_t plan, const void* f, void* u, int nrhs, cudaStream_t stream);
+
+/* Size in bytes of the scratch array of dfmm_apply_noalloc. */
+int64_t dfmm_noalloc_capacity(void);
+
 /* Per-kernel timing of applies, measured with CUDA events that the library
  * records on the apply stream around each of its launches.
  *   enable != 0 : start recording on `stream` (out may be NULL).

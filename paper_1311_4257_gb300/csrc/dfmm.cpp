@@ -25,6 +25,7 @@
 
 #include "apply.h"
 #include "common.h"
+#include "internal.h"
 #include "operators.h"
 #include "skeleton.h"
 #include "tree.h"
@@ -105,6 +106,7 @@ struct M2PGroup {
 
 struct Workspace {
   int nrhs = 0;
+  bool external = false;   // buffers carved from caller-provided memory
   DevArena ar;
   float2 *fs = nullptr, *us = nullptr, *p2m = nullptr, *p2l = nullptr;
   std::vector<float2*> S, T;                            // per level (LF or HF states)
@@ -946,6 +948,7 @@ std::pair<int4*, int64_t> tiles_for(Workspace* W, const GemmPlan& g, int nrhs, c
   auto key = std::make_pair((const void*)&g, nrhs);
   auto it = W->tiles.find(key);
   if (it != W->tiles.end()) return it->second;
+  if (W->external) throw Error(DFMM_ERR_INVALID, "work tiles missing from the carved workspace");
   int per = std::max(1, 64 / nrhs);
   std::vector<int4> t;
   for (const int4& grp : g.groups)
@@ -991,8 +994,9 @@ struct Runner {
   }
 };
 
-void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_t s, int64_t* count = nullptr) {
-  Workspace* W = count ? nullptr : get_workspace(P, s, nrhs);
+void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_t s, int64_t* count = nullptr,
+               Workspace* ext = nullptr) {
+  Workspace* W = count ? nullptr : (ext ? ext : get_workspace(P, s, nrhs));
   Runner R{P, W, s, nrhs, count};
   const int64_t N = P->N;
   const int nl = P->nl;
@@ -1117,6 +1121,75 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
   R.launch(F_PERMUTE, 0.0, 20.0 * N * nrhs, [&] { launch_permute_out(W->us, P->perm, N, nrhs, u, s); });
 }
 
+// Every translation stage of the plan, for laying out work tiles.
+std::vector<const GemmPlan*> all_gemms(dfmm_plan_s* P) {
+  std::vector<const GemmPlan*> v;
+  for (auto& F : P->lf) { v.push_back(&F.m2m); v.push_back(&F.l2l); v.push_back(&F.v); v.push_back(&F.p2m); v.push_back(&F.p2l); }
+  for (auto& H : P->hf) { v.push_back(&H.m2m); v.push_back(&H.m2l); v.push_back(&H.l2l); }
+  return v;
+}
+
+// Lays out the whole workspace of an apply with nrhs right-hand sides inside
+// [base, base + bytes): state buffers, staging buffers and the work tiles of
+// every stage (copied in on `s`).  No device memory is allocated.
+void carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaStream_t s, Workspace& W) {
+  size_t off = 0;
+  auto take = [&](size_t n) -> char* {
+    off = (off + 255) & ~(size_t)255;
+    char* p = base + off;
+    off += std::max<size_t>(n, 1);
+    return p;
+  };
+  const int64_t N = P->N;
+  W.external = true;
+  W.nrhs = nrhs;
+  W.fs = (float2*)take((size_t)N * nrhs * 8);
+  W.us = (float2*)take((size_t)N * nrhs * 8);
+  W.zero.push_back({W.us, (size_t)N * nrhs * 8});
+  W.S.assign(P->nl, nullptr);
+  W.T.assign(P->nl, nullptr);
+  size_t p2m_rows = 1, p2l_rows = 1;
+  for (int l = 0; l < P->nl; ++l) {
+    if (l >= P->l_lf0) {
+      size_t b = (size_t)P->lf[l].nbox * nrhs * P->lf[l].R * 8;
+      W.S[l] = (float2*)take(b);
+      W.T[l] = (float2*)take(b);
+      W.zero.push_back({W.S[l], b});
+      W.zero.push_back({W.T[l], b});
+      p2m_rows = std::max(p2m_rows, (size_t)P->lf[l].n_p2m * 2 * P->lf[l].R);
+      p2l_rows = std::max(p2l_rows, (size_t)P->lf[l].n_p2l * 2 * P->lf[l].R);
+    } else if (P->l_top >= 0 && l >= P->l_top) {
+      size_t so = P->hf[l].out_keys.size(), si = P->hf[l].in_keys.size();
+      size_t R = P->hf[l].R;
+      if (so) { W.S[l] = (float2*)take(so * nrhs * R * 8); W.zero.push_back({W.S[l], so * nrhs * R * 8}); }
+      if (si) { W.T[l] = (float2*)take(si * nrhs * R * 8); W.zero.push_back({W.T[l], si * nrhs * R * 8}); }
+    }
+  }
+  W.p2m = (float2*)take(p2m_rows * nrhs * 8);
+  W.p2l = (float2*)take(p2l_rows * nrhs * 8);
+  W.status = (unsigned*)take(4);
+  W.zero.push_back({W.status, 4});
+  const int per = std::max(1, 64 / nrhs);
+  std::vector<std::pair<const GemmPlan*, std::vector<int4>>> tl;
+  for (const GemmPlan* g : all_gemms(P)) {
+    if (g->npairs == 0) continue;
+    std::vector<int4> t;
+    for (const int4& grp : g->groups)
+      for (int q = 0; q < grp.z; q += per) t.push_back(make_int4(grp.x, grp.y + q, std::min(per, grp.z - q), 0));
+    tl.push_back({g, std::move(t)});
+  }
+  std::vector<int4*> dst(tl.size());
+  for (size_t k = 0; k < tl.size(); ++k) dst[k] = (int4*)take(tl[k].second.size() * sizeof(int4));
+  if (off > bytes)
+    throw Error(DFMM_ERR_UNSUPPORTED, "apply needs " + std::to_string(off) + " bytes of scratch, more than the " +
+                                          std::to_string(bytes) + " bytes of the static scratch array");
+  for (size_t k = 0; k < tl.size(); ++k) {
+    DFMM_CUDA(cudaMemcpyAsync(dst[k], tl[k].second.data(), tl[k].second.size() * sizeof(int4),
+                              cudaMemcpyHostToDevice, s));
+    W.tiles[std::make_pair((const void*)tl[k].first, nrhs)] = {dst[k], (int64_t)tl[k].second.size()};
+  }
+}
+
 template <class F>
 int guarded(F&& fn) {
   try {
@@ -1131,6 +1204,28 @@ int guarded(F&& fn) {
 }
 
 }  // namespace
+
+namespace dfmm {
+
+int set_error(int code, const char* msg) { return fail(code, msg); }
+
+int apply_with_scratch(dfmm_plan_s* P, const void* f, void* u, int nrhs, cudaStream_t stream, void* scratch,
+                       size_t bytes) {
+  return guarded([&]() -> int {
+    if (!P || !f || !u) return fail(DFMM_ERR_INVALID, "null argument");
+    if (nrhs < 1 || nrhs > 64) return fail(DFMM_ERR_INVALID, "nrhs must be in [1, 64]");
+    if (f == u) return fail(DFMM_ERR_INVALID, "f and u must not alias");
+    int dev = -1;
+    DFMM_CUDA(cudaGetDevice(&dev));
+    if (dev != P->device) return fail(DFMM_ERR_INVALID, "the plan belongs to another device");
+    Workspace W;
+    carve_workspace(P, nrhs, (char*)scratch, bytes, stream, W);
+    run_apply(P, (const float2*)f, (float2*)u, nrhs, stream, nullptr, &W);
+    return DFMM_OK;
+  });
+}
+
+}  // namespace dfmm
 
 // --------------------------------------------------------------- C ABI ---
 

@@ -1,0 +1,19 @@
+// Entry points shared between translation units of the library (not part of
+// the C ABI).
+#pragma once
+#include <cstddef>
+
+#include "dfmm.h"
+
+namespace dfmm {
+
+// Records `msg` as the calling thread's last error and returns `code`.
+int set_error(int code, const char* msg);
+
+// The matvec of dfmm_apply with every per-apply buffer (states, staging
+// buffers, work tiles) laid out inside the caller-provided device memory
+// [scratch, scratch + bytes); no device memory is allocated.
+int apply_with_scratch(dfmm_plan_s* plan, const void* f, void* u, int nrhs, cudaStream_t stream, void* scratch,
+                       size_t bytes);
+
+}  // namespace dfmm
