@@ -30,6 +30,8 @@ METRIC = "FMM matvec points*RHS/s at <=1e-5 rel err, chosen vs plain; p50/p99 la
 WORKLOADS = {
     "sphere_K64": dict(K=64.0, seed=1, eps=1e-5, desc="sphere diameter 64, N=1,286,796 (seed 1), eps 1e-5"),
     "sphere_K8": dict(K=8.0, seed=0, eps=1e-6, desc="sphere diameter 8, N=20,106 (seed 0), eps 1e-6"),
+    "sphere_K16": dict(K=16.0, seed=1, eps=1e-5, desc="sphere diameter 16, N=80,424 (seed 1), eps 1e-5"),
+    "sphere_K32": dict(K=32.0, seed=1, eps=1e-5, desc="sphere diameter 32, N=321,699 (seed 1), eps 1e-5"),
 }
 
 
@@ -161,7 +163,7 @@ def run_ours(args, wl):
     nrhs = args.nrhs
     f = workloads.densities(N, nrhs, wl["seed"])
     t0 = time.perf_counter()
-    plan = Plan(p, K, wl["eps"], cache_dir=args.cache_dir)
+    plan = Plan(p, K, wl["eps"], cache_dir=args.cache_dir, m2l_mode={"auto": 0, "fp32": 1, "tc": 2}[args.form])
     plan_s = time.perf_counter() - t0
     st = plan.stats()
     fd = torch.as_tensor(f.astype(np.complex64), device="cuda")
@@ -228,17 +230,29 @@ def run_ours(args, wl):
     d = prof[dom]
     launches = d["launches"]
     achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
-    roofline = {"kernel": "gemm_stage_kernel (" + dom + ")", "bound": "alu", "achieved": achieved,
-                "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["fp32_tflops"],
-                "peak_source": "FP32 CUDA-core peak 152 SM x 128 lanes x 2 x %.0f MHz (%s clock)" % (
-                    pk["sm_max_mhz"], pk["source"]),
-                "traffic": traffic_for(dom), "ms_per_launch": d["ms"] / launches,
-                "flops_per_launch": d["flops"] / launches}
+    tc = (args.form == "tc") or (args.form == "auto" and wl["eps"] >= 1e-5)
+    if tc:
+        # split TF32 issues 4 MMAs per useful multiply-add; peak = measured
+        # BF16 dense x (nominal TF32 / BF16 = 1.1 / 2.25) per issued flop
+        tf32 = pk["bf16_tflops"] * 1.1 / 2.25
+        roofline = {"kernel": "gemm_tc_kernel (" + dom + ")", "bound": "tensor", "achieved": achieved,
+                    "peak": tf32 / 4, "unit": "TFLOP/s", "frac": achieved / (tf32 / 4),
+                    "issued_tflops": 4 * achieved, "issued_frac_of_tf32_peak": 4 * achieved / tf32,
+                    "peak_source": "measured bf16 dense %.1f TF/s x 1.1/2.25 (TF32), / 4 MMAs per useful product"
+                                   % pk["bf16_tflops"]}
+    else:
+        roofline = {"kernel": "gemm_stage_kernel (" + dom + ")", "bound": "alu", "achieved": achieved,
+                    "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["fp32_tflops"],
+                    "peak_source": "FP32 CUDA-core peak 152 SM x 128 lanes x 2 x %.0f MHz (%s clock)" % (
+                        pk["sm_max_mhz"], pk["source"])}
+    roofline.update({"traffic": traffic_for(dom), "ms_per_launch": d["ms"] / launches,
+                     "flops_per_launch": d["flops"] / launches})
     out = {"metric": METRIC, "value": value, "unit": "points*RHS/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "c64 (fp32)", "data": "synthetic",
            "config": {"workload": wl["desc"], "N": N, "K": K, "eps": wl["eps"], "nrhs": nrhs,
-                      "form": "plain: FP32 CUDA-core translations, one stream", "parallelism": "replicas" if world > 1 else "1 gpu",
+                      "form": "tensor cores (tcgen05 split TF32)" if tc else "FP32 CUDA cores",
+                      "parallelism": "replicas" if world > 1 else "1 gpu",
                       "l2": "inputs larger than L2 (plan %.1f GB resident, states re-zeroed each step)" % (st["plan_bytes"] / 1e9),
                       "plan_seconds": plan_s},
            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
@@ -246,6 +260,35 @@ def run_ours(args, wl):
                    "d2h_bytes_per_step": 8 * N * nrhs},
            "gpu_launches": plan.launches(nrhs) * args.steps,
            "clocks": clocks, "roofline": roofline, "stages": stages}
+    if args.compare and rank == 0:
+        # the plain form (FP32 CUDA cores, one RHS) and the batched chosen form (16 RHS)
+        plain = Plan(p, K, wl["eps"], cache_dir=args.cache_dir, m2l_mode=1)
+        for _ in range(2):
+            plain.apply(fd, ud)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(5):
+            plain.apply(fd, ud)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1) / 5
+        del plain
+        f16 = torch.as_tensor(workloads.densities(N, 16, wl["seed"] + 1).astype(np.complex64), device="cuda")
+        u16 = torch.empty_like(f16)
+        for _ in range(2):
+            plan.apply(f16, u16)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(5):
+            plan.apply(f16, u16)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bms = e0.elapsed_time(e1) / 5
+        out["plain_vs_chosen"] = {"plain_fp32_nrhs1": N / (pms / 1e3), "chosen_nrhs1": value,
+                                  "chosen_nrhs16": 16 * N / (bms / 1e3),
+                                  "speedup_nrhs1": value / (N / (pms / 1e3)),
+                                  "speedup_nrhs16": 16 * N / (bms / 1e3) / (N / (pms / 1e3)),
+                                  "unit": "points*RHS/s"}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         t, ref, dt = cpu_oracle_sample(p, f, args.ref_targets, 1001)
         u = ud.cpu().numpy()
@@ -271,6 +314,8 @@ def main():
     ap.add_argument("--ref-targets", type=int, default=300)
     ap.add_argument("--cache-dir", default=os.path.join(tempfile.gettempdir(), "dfmm_cache"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--form", default="auto", choices=["auto", "fp32", "tc"])
+    ap.add_argument("--compare", action="store_true", help="also time the plain FP32 form and 16 RHS")
     args = ap.parse_args()
     os.makedirs(args.cache_dir, exist_ok=True)
     wl = WORKLOADS[args.workload]

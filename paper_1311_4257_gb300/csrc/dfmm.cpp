@@ -48,6 +48,7 @@ struct GemmPlan {
   int2* pairs = nullptr;
   int64_t npairs = 0;
   int fam = 0;                     // profiling family
+  float* img = nullptr;            // tensor-core operator image (tensor form only)
   double flops_rhs = 0;            // algorithmic flops per right-hand side
   double bytes_fixed = 0;          // operators (bytes once per launch)
   double bytes_rhs = 0;            // unique source rows + target rows (read and write), per rhs
@@ -109,9 +110,10 @@ struct Workspace {
   bool external = false;   // buffers carved from caller-provided memory
   DevArena ar;
   float2 *fs = nullptr, *us = nullptr, *p2m = nullptr, *p2l = nullptr;
+  float *ahi = nullptr, *alo = nullptr;                 // split source buffer (tensor form)
   std::vector<float2*> S, T;                            // per level (LF or HF states)
   std::vector<std::pair<void*, size_t>> zero;           // reset before each apply
-  std::map<std::pair<const void*, int>, std::pair<int4*, int64_t>> tiles;
+  std::map<std::pair<const void*, int>, std::pair<int4*, int64_t>> tiles;   // key (stage, nrhs * 1024 + columns)
   float2 *f_dev = nullptr, *u_dev = nullptr;            // staging for host applies
   unsigned* status = nullptr;
   bool prof = false;
@@ -455,7 +457,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
   for (int l = (has_hf ? P->l_top : P->l_lf0); l < nl; ++l) {
     int rmax = 0;
     for (int c : level_cells[l]) rmax = std::max(rmax, P->reps->get(LV[l].w, c).r);
-    int R = round_up(std::max(rmax, 4), 4);
+    int R = round_up(std::max(rmax, 8), 8);
     if (R > 256) throw Error(DFMM_ERR_UNSUPPORTED, "representation rank above 256");
     if (l <= P->l1) P->hf[l].R = R;
     else { P->lf[l].R = R; P->lf[l].r = rmax; }
@@ -904,6 +906,24 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
 
 // ------------------------------------------------------------------- apply ---
 
+// Largest source buffer of a translation stage, in complex elements per RHS
+// (the tensor form splits it into TF32 hi / lo float arrays).
+int64_t max_source_elems(const dfmm_plan_s* P) {
+  int64_t m = 0;
+  for (int l = 0; l < P->nl; ++l) {
+    if (l >= P->l_lf0) {
+      const LFLevel& F = P->lf[l];
+      m = std::max(m, F.nbox * (int64_t)F.R);
+      m = std::max(m, F.n_p2m * 2 * (int64_t)F.R);
+      m = std::max(m, F.n_p2l * 2 * (int64_t)F.R);
+    } else if (P->l_top >= 0 && l >= P->l_top) {
+      const HFLevel& H = P->hf[l];
+      m = std::max(m, (int64_t)std::max(H.out_keys.size(), H.in_keys.size()) * H.R);
+    }
+  }
+  return m;
+}
+
 Workspace* get_workspace(dfmm_plan_s* P, cudaStream_t s, int nrhs) {
   std::lock_guard<std::mutex> g(P->ws_mu);
   auto& slot = P->ws[s];
@@ -939,17 +959,23 @@ Workspace* get_workspace(dfmm_plan_s* P, cudaStream_t s, int nrhs) {
   }
   W->p2m = ar.alloc<float2>(p2m_rows * nrhs);
   W->p2l = ar.alloc<float2>(p2l_rows * nrhs);
+  if (P->opt.m2l_mode == 2) {
+    int64_t e = max_source_elems(P) * nrhs * 2;
+    W->ahi = ar.alloc<float>(e);
+    W->alo = ar.alloc<float>(e);
+  }
   W->status = ar.alloc<unsigned>(1);
+  W->zero.push_back({W->status, 4});   // reset by every apply; read by dfmm_sync_status
   DFMM_CUDA(cudaMemsetAsync(W->status, 0, 4, s));
   return W;
 }
 
-std::pair<int4*, int64_t> tiles_for(Workspace* W, const GemmPlan& g, int nrhs, cudaStream_t s) {
-  auto key = std::make_pair((const void*)&g, nrhs);
+std::pair<int4*, int64_t> tiles_for(Workspace* W, const GemmPlan& g, int nrhs, int cols, cudaStream_t s) {
+  auto key = std::make_pair((const void*)&g, nrhs * 1024 + cols);
   auto it = W->tiles.find(key);
   if (it != W->tiles.end()) return it->second;
   if (W->external) throw Error(DFMM_ERR_INVALID, "work tiles missing from the carved workspace");
-  int per = std::max(1, 64 / nrhs);
+  int per = std::max(1, cols / nrhs);
   std::vector<int4> t;
   for (const int4& grp : g.groups)
     for (int p = 0; p < grp.z; p += per) t.push_back(make_int4(grp.x, grp.y + p, std::min(per, grp.z - p), 0));
@@ -973,10 +999,11 @@ struct Runner {
     fn();
   }
 
-  void gemm(const GemmPlan& g, const float2* src, int src_ld, float2* dst, int dst_ld) {
+  void gemm(const GemmPlan& g, const float2* src, int src_ld, int64_t src_rows, float2* dst, int dst_ld) {
     if (g.npairs == 0) return;
-    if (count) { ++*count; return; }
-    auto t = tiles_for(W, g, nrhs, s);
+    if (count) { count[0] += (P->opt.m2l_mode == 2) ? 2 : 1; return; }
+    const bool tc = P->opt.m2l_mode == 2;
+    auto t = tiles_for(W, g, nrhs, tc ? gemm_tc_columns() : 64, s);
     GemmArgs a;
     a.ops = g.ops;
     a.M = g.M;
@@ -990,7 +1017,13 @@ struct Runner {
     a.dst_ld = dst_ld;
     a.nrhs = nrhs;
     ProfScope ps(W, s, g.fam, g.flops_rhs * nrhs, g.bytes_fixed + g.bytes_rhs * nrhs);
-    launch_gemm_stage(a, s);
+    if (tc) {
+      launch_split(src, src_rows * nrhs, src_ld, W->ahi, W->alo, s);
+      TcArgs targs{g.img, W->ahi, W->alo};
+      launch_gemm_stage_tc(a, targs, W->status, s);
+    } else {
+      launch_gemm_stage(a, s);
+    }
   }
 };
 
@@ -1026,33 +1059,35 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
         a.nrhs = nrhs;
         launch_p2c(a, s);
       });
-      R.gemm(F.p2m, count ? nullptr : W->p2m, 2 * F.R, S(l), F.R);
+      R.gemm(F.p2m, count ? nullptr : W->p2m, 2 * F.R, F.n_p2m, S(l), F.R);
     }
-    if (l + 1 < nl) R.gemm(F.m2m, S(l + 1), P->lf[l + 1].R, S(l), F.R);
+    if (l + 1 < nl) R.gemm(F.m2m, S(l + 1), P->lf[l + 1].R, P->lf[l + 1].nbox, S(l), F.R);
   }
   // 2. HF upward
   if (P->l_top >= 0) {
     for (int l = P->l1; l >= P->l_top; --l) {
       HFLevel& H = P->hf[l];
       int sld = (l == P->l1) ? P->lf[l + 1].R : P->hf[l + 1].R;
-      R.gemm(H.m2m, S(l + 1), sld, S(l), H.R);
+      int64_t srows = (l == P->l1) ? P->lf[l + 1].nbox : (int64_t)P->hf[l + 1].out_keys.size();
+      R.gemm(H.m2m, S(l + 1), sld, srows, S(l), H.R);
     }
     // 3. HF downward: L2L from the parent level, then M2L
     for (int l = P->l_top; l <= P->l1; ++l) {
       HFLevel& H = P->hf[l];
-      if (l > P->l_top) R.gemm(H.l2l, T(l - 1), P->hf[l - 1].R, T(l), H.R);
-      R.gemm(H.m2l, S(l), H.R, T(l), H.R);
+      if (l > P->l_top) R.gemm(H.l2l, T(l - 1), P->hf[l - 1].R, (int64_t)P->hf[l - 1].in_keys.size(), T(l), H.R);
+      R.gemm(H.m2l, S(l), H.R, (int64_t)H.out_keys.size(), T(l), H.R);
     }
   }
   // 4. LF downward
   for (int l = P->l_lf0; l < nl; ++l) {
     LFLevel& F = P->lf[l];
     if (l == P->l_lf0) {
-      if (P->l_top >= 0) R.gemm(F.l2l, T(P->l1), P->hf[P->l1].R, T(l), F.R);
+      if (P->l_top >= 0)
+        R.gemm(F.l2l, T(P->l1), P->hf[P->l1].R, (int64_t)P->hf[P->l1].in_keys.size(), T(l), F.R);
     } else {
-      R.gemm(F.l2l, T(l - 1), P->lf[l - 1].R, T(l), F.R);
+      R.gemm(F.l2l, T(l - 1), P->lf[l - 1].R, P->lf[l - 1].nbox, T(l), F.R);
     }
-    R.gemm(F.v, S(l), F.R, T(l), F.R);
+    R.gemm(F.v, S(l), F.R, F.nbox, T(l), F.R);
     if (F.n_p2l) {
       double ev = (double)F.npts_x * 2 * F.r;
       R.launch(F_P2L_EVAL, ev * (16 + 8.0 * nrhs), F.npts_x * (16.0 + 8.0 * nrhs) + F.n_p2l * 2.0 * F.R * 8 * nrhs, [&] {
@@ -1069,7 +1104,7 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
         a.nrhs = nrhs;
         launch_p2c(a, s);
       });
-      R.gemm(F.p2l, count ? nullptr : W->p2l, 2 * F.R, T(l), F.R);
+      R.gemm(F.p2l, count ? nullptr : W->p2l, 2 * F.R, F.n_p2l, T(l), F.R);
     }
   }
   // 5. L2P at every leaf, M2P over the W list
@@ -1167,9 +1202,15 @@ void carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaStr
   }
   W.p2m = (float2*)take(p2m_rows * nrhs * 8);
   W.p2l = (float2*)take(p2l_rows * nrhs * 8);
+  if (P->opt.m2l_mode == 2) {
+    size_t e = (size_t)max_source_elems(P) * nrhs * 2;
+    W.ahi = (float*)take(e * 4);
+    W.alo = (float*)take(e * 4);
+  }
   W.status = (unsigned*)take(4);
   W.zero.push_back({W.status, 4});
-  const int per = std::max(1, 64 / nrhs);
+  const int cols = P->opt.m2l_mode == 2 ? gemm_tc_columns() : 64;
+  const int per = std::max(1, cols / nrhs);
   std::vector<std::pair<const GemmPlan*, std::vector<int4>>> tl;
   for (const GemmPlan* g : all_gemms(P)) {
     if (g->npairs == 0) continue;
@@ -1186,8 +1227,20 @@ void carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaStr
   for (size_t k = 0; k < tl.size(); ++k) {
     DFMM_CUDA(cudaMemcpyAsync(dst[k], tl[k].second.data(), tl[k].second.size() * sizeof(int4),
                               cudaMemcpyHostToDevice, s));
-    W.tiles[std::make_pair((const void*)tl[k].first, nrhs)] = {dst[k], (int64_t)tl[k].second.size()};
+    W.tiles[std::make_pair((const void*)tl[k].first, nrhs * 1024 + cols)] = {dst[k], (int64_t)tl[k].second.size()};
   }
+}
+
+// Operator images of every translation stage for the tensor-core form.
+void build_images(dfmm_plan_s* P, cudaStream_t s) {
+  for (const GemmPlan* gc : all_gemms(P)) {
+    GemmPlan* g = const_cast<GemmPlan*>(gc);
+    if (g->npairs == 0 || g->nops == 0) continue;
+    g->img = P->ar.alloc<float>(tc_image_floats(g->M, g->Kd, g->nops));
+    build_tc_image(g->ops, g->M, g->Kd, g->nops, g->img, s);
+  }
+  DFMM_CUDA(cudaStreamSynchronize(s));
+  P->stats.plan_bytes = (int64_t)P->ar.bytes();
 }
 
 template <class F>
@@ -1254,6 +1307,10 @@ int dfmm_plan(const double* points, int64_t N, double K, double eps, const dfmm_
     if (o.sample_far <= 0) o.sample_far = 4096;
     if (o.sketch_rows <= 0) o.sketch_rows = 400;
     if (!(o.eps_op_factor > 0)) o.eps_op_factor = 0.3;
+    if (o.m2l_mode < 0 || o.m2l_mode > 2) return fail(DFMM_ERR_INVALID, "m2l_mode must be 0, 1 or 2");
+    // automatic form: split-TF32 tensor cores add about 3e-6 relative error,
+    // so they serve eps >= 1e-5; tighter tolerances use FP32 CUDA cores
+    if (o.m2l_mode == 0) o.m2l_mode = eps >= 1e-5 ? 2 : 1;
     P->opt = o;
     P->eps_op = eps * o.eps_op_factor;
     P->stats.N = N;
@@ -1265,6 +1322,7 @@ int dfmm_plan(const double* points, int64_t N, double K, double eps, const dfmm_
     DFMM_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     struct SG { cudaStream_t s; ~SG() { cudaStreamDestroy(s); } } sg{s};
     build_plan(P.get(), points, s);
+    if (P->opt.m2l_mode == 2) build_images(P.get(), s);
     DFMM_CUDA(cudaStreamSynchronize(s));
     *out = P.release();
     return DFMM_OK;

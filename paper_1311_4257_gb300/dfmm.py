@@ -121,7 +121,7 @@ class Plan:
 
     def __init__(self, points, K: float, eps: float, leaf_max: int = 0, sample_box: int = 0, sample_far: int = 0,
                  sketch_rows: int = 0, eps_op_factor: float = 0.0, host_threads: int = 0,
-                 cache_dir: str | None = None):
+                 cache_dir: str | None = None, m2l_mode: int = 0):
         import torch
         if not (isinstance(points, torch.Tensor) and points.is_cuda):
             points = torch.as_tensor(np.ascontiguousarray(points, dtype=np.float64), device="cuda")
@@ -131,7 +131,7 @@ class Plan:
         self.N = int(points.shape[0])
         self.K = float(K)
         self.eps = float(eps)
-        o = Options(leaf_max, sample_box, sample_far, sketch_rows, eps_op_factor, 0, host_threads,
+        o = Options(leaf_max, sample_box, sample_far, sketch_rows, eps_op_factor, m2l_mode, host_threads,
                     cache_dir.encode() if cache_dir else None)
         h = ctypes.c_void_p()
         _check(lib().dfmm_plan(points.data_ptr(), self.N, self.K, self.eps, ctypes.byref(o), ctypes.byref(h)))

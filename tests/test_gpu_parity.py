@@ -165,3 +165,15 @@ def test_config2_sphere_k64_sampled_targets():
     t = np.random.default_rng(1001).choice(p.shape[0], 200, replace=False)
     ud = OD.direct(p, f, t, chunk=8)
     assert OD.rel_err(u[:, t], ud) <= 1e-5
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_tensor_core_form_matches_cuda_core_form(nrhs):
+    """The tcgen05 split-TF32 translations agree with the FP32 CUDA-core ones."""
+    p = workloads.sphere(8.0, 0)
+    f = workloads.densities(p.shape[0], nrhs, 3)
+    u_tc = _apply(_plan(p, 8.0, 1e-5, m2l_mode=2), f)
+    u_fp = _apply(_plan(p, 8.0, 1e-5, m2l_mode=1), f)
+    assert OD.rel_err(u_tc, u_fp) < 5e-6
+    t = np.arange(0, p.shape[0], 7)
+    assert OD.rel_err(u_tc[:, t], OD.direct(p, f, t)) < 1e-5
