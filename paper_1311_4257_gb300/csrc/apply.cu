@@ -25,6 +25,15 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// fire-and-forget vector adds to global memory (no value returned)
+__device__ __forceinline__ void red_add4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+               : "memory");
+}
+__device__ __forceinline__ void red_add2(float* p, float a, float b) {
+  asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+
 __global__ __launch_bounds__(256) void gemm_stage_kernel(GemmArgs a) {
   __shared__ float2 As[BK][BM + 1];
   __shared__ float2 Bs[BK][BN + 1];
@@ -90,12 +99,12 @@ __global__ __launch_bounds__(256) void gemm_stage_kernel(GemmArgs a) {
     float2* d = dstp[c] + row0 + ty * 4;
     int r = row0 + ty * 4;
     if (r + 3 < a.M) {
-      atomicAdd((float4*)d, make_float4(acc[0][j].x, acc[0][j].y, acc[1][j].x, acc[1][j].y));
-      atomicAdd((float4*)(d + 2), make_float4(acc[2][j].x, acc[2][j].y, acc[3][j].x, acc[3][j].y));
+      red_add4((float*)d, acc[0][j].x, acc[0][j].y, acc[1][j].x, acc[1][j].y);
+      red_add4((float*)(d + 2), acc[2][j].x, acc[2][j].y, acc[3][j].x, acc[3][j].y);
     } else {
 #pragma unroll
       for (int i = 0; i < 4; ++i)
-        if (r + i < a.M) atomicAdd(d + i, acc[i][j]);
+        if (r + i < a.M) red_add2((float*)(d + i), acc[i][j].x, acc[i][j].y);
     }
   }
 }

@@ -40,6 +40,7 @@ struct TcArgs {
 };
 void launch_gemm_stage_tc(const GemmArgs& a, const TcArgs& t, unsigned* status, cudaStream_t s);
 int gemm_tc_columns();
+bool gemm_tc_supported(int M, int Kd);
 int64_t tc_image_floats(int M, int Kd, int nops);
 void build_tc_image(const float2* ops, int M, int Kd, int nops, float* img, cudaStream_t s);
 void launch_split(const float2* x, int64_t rows, int ld, float* hi, float* lo, cudaStream_t s);

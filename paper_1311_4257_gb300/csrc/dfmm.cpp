@@ -1001,8 +1001,8 @@ struct Runner {
 
   void gemm(const GemmPlan& g, const float2* src, int src_ld, int64_t src_rows, float2* dst, int dst_ld) {
     if (g.npairs == 0) return;
-    if (count) { count[0] += (P->opt.m2l_mode == 2) ? 2 : 1; return; }
-    const bool tc = P->opt.m2l_mode == 2;
+    if (count) { count[0] += (P->opt.m2l_mode == 2 && gemm_tc_supported(g.M, g.Kd)) ? 2 : 1; return; }
+    const bool tc = P->opt.m2l_mode == 2 && gemm_tc_supported(g.M, g.Kd);
     auto t = tiles_for(W, g, nrhs, tc ? gemm_tc_columns() : 64, s);
     GemmArgs a;
     a.ops = g.ops;
@@ -1209,11 +1209,13 @@ void carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaStr
   }
   W.status = (unsigned*)take(4);
   W.zero.push_back({W.status, 4});
-  const int cols = P->opt.m2l_mode == 2 ? gemm_tc_columns() : 64;
-  const int per = std::max(1, cols / nrhs);
   std::vector<std::pair<const GemmPlan*, std::vector<int4>>> tl;
+  std::vector<int> tl_cols;
   for (const GemmPlan* g : all_gemms(P)) {
     if (g->npairs == 0) continue;
+    const int cols = (P->opt.m2l_mode == 2 && gemm_tc_supported(g->M, g->Kd)) ? gemm_tc_columns() : 64;
+    const int per = std::max(1, cols / nrhs);
+    tl_cols.push_back(cols);
     std::vector<int4> t;
     for (const int4& grp : g->groups)
       for (int q = 0; q < grp.z; q += per) t.push_back(make_int4(grp.x, grp.y + q, std::min(per, grp.z - q), 0));
@@ -1227,7 +1229,7 @@ void carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaStr
   for (size_t k = 0; k < tl.size(); ++k) {
     DFMM_CUDA(cudaMemcpyAsync(dst[k], tl[k].second.data(), tl[k].second.size() * sizeof(int4),
                               cudaMemcpyHostToDevice, s));
-    W.tiles[std::make_pair((const void*)tl[k].first, nrhs * 1024 + cols)] = {dst[k], (int64_t)tl[k].second.size()};
+    W.tiles[std::make_pair((const void*)tl[k].first, nrhs * 1024 + tl_cols[k])] = {dst[k], (int64_t)tl[k].second.size()};
   }
 }
 
@@ -1235,7 +1237,7 @@ void carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaStr
 void build_images(dfmm_plan_s* P, cudaStream_t s) {
   for (const GemmPlan* gc : all_gemms(P)) {
     GemmPlan* g = const_cast<GemmPlan*>(gc);
-    if (g->npairs == 0 || g->nops == 0) continue;
+    if (g->npairs == 0 || g->nops == 0 || !gemm_tc_supported(g->M, g->Kd)) continue;
     g->img = P->ar.alloc<float>(tc_image_floats(g->M, g->Kd, g->nops));
     build_tc_image(g->ops, g->M, g->Kd, g->nops, g->img, s);
   }

@@ -350,6 +350,8 @@ __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcAr
 
 int gemm_tc_columns() { return TC_M; }
 
+bool gemm_tc_supported(int M, int Kd) { return M % 8 == 0 && Kd % 8 == 0; }
+
 int64_t tc_image_floats(int M, int Kd, int nops) { return (int64_t)nops * 2 * (2 * M) * (2 * Kd); }
 
 void build_tc_image(const float2* ops, int M, int Kd, int nops, float* img, cudaStream_t s) {
@@ -371,7 +373,7 @@ void launch_split(const float2* x, int64_t rows, int ld, float* hi, float* lo, c
 
 void launch_gemm_stage_tc(const GemmArgs& a, const TcArgs& t, unsigned* status, cudaStream_t s) {
   if (a.ntiles == 0) return;
-  if (a.M % 8 != 0 || a.Kd % 8 != 0 || a.src_ld != a.Kd)
+  if (!gemm_tc_supported(a.M, a.Kd) || a.src_ld != a.Kd)
     throw Error(-5, "tensor-core stage needs ranks padded to a multiple of 8 and dense source rows");
   static bool attr = false;
   if (!attr) {
