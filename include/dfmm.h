@@ -61,7 +61,7 @@ typedef struct {
   double eps_op_factor;    /* [0.3] skeleton tolerance = eps * factor */
   int32_t m2l_mode;        /* [0] translations on: 0 = automatic (tensor cores if eps >= 1e-5, else
                               FP32 CUDA cores), 1 = FP32 CUDA cores, 2 = tensor cores (tcgen05,
-                              split TF32; adds about 3e-6 relative error) */
+                              scaled FP16 hi/lo split; adds about 2e-6 relative error) */
   int32_t host_threads;    /* [0 = all cores] threads for the skeleton precompute */
   const char* cache_dir;   /* [NULL = no disk cache] directory for skeleton files */
 } dfmm_options;

@@ -2,6 +2,8 @@
 #pragma once
 #include <cstdint>
 
+#include <cuda_fp16.h>
+
 #include "common.h"
 
 namespace dfmm {
@@ -29,21 +31,24 @@ struct GemmArgs {
 
 void launch_gemm_stage(const GemmArgs& a, cudaStream_t s);
 
-// Tensor-core form (tcgen05, split TF32) of the same stage; M and Kd must be
-// multiples of 8, source rows dense (src_ld == Kd); tiles hold up to
-// gemm_tc_columns() columns.  img: operator image (build_tc_image); src_hi /
-// src_lo: the source buffer split by launch_split.
+// Tensor-core form (tcgen05, scaled FP16 split) of the same stage; M and Kd
+// must be multiples of 8, source rows dense (src_ld == Kd); tiles hold up to
+// gemm_tc_columns() columns.  img / op_scale: operator image and per-operator
+// power-of-two scales (build_tc_image); src_hi / src_lo / src_scale: the
+// source buffer split by launch_split (one scale per source row).
 struct TcArgs {
-  const float* img;
-  const float* src_hi;
-  const float* src_lo;
+  const __half* img;
+  const float* op_scale;
+  const __half* src_hi;
+  const __half* src_lo;
+  const float* src_scale;
 };
 void launch_gemm_stage_tc(const GemmArgs& a, const TcArgs& t, unsigned* status, cudaStream_t s);
 int gemm_tc_columns();
 bool gemm_tc_supported(int M, int Kd);
-int64_t tc_image_floats(int M, int Kd, int nops);
-void build_tc_image(const float2* ops, int M, int Kd, int nops, float* img, cudaStream_t s);
-void launch_split(const float2* x, int64_t rows, int ld, float* hi, float* lo, cudaStream_t s);
+int64_t tc_image_elems(int M, int Kd, int nops);
+void build_tc_image(const float2* ops, int M, int Kd, int nops, __half* img, float* scale, cudaStream_t s);
+void launch_split(const float2* x, int64_t rows, int ld, __half* hi, __half* lo, float* scale, cudaStream_t s);
 
 // Permutes: fs[k][rhs] = f[rhs][perm[k]];  u[rhs][perm[k]] = us[k][rhs].
 void launch_permute_in(const float2* f, const int32_t* perm, int64_t N, int nrhs, float2* fs, cudaStream_t s);

@@ -48,7 +48,8 @@ struct GemmPlan {
   int2* pairs = nullptr;
   int64_t npairs = 0;
   int fam = 0;                     // profiling family
-  float* img = nullptr;            // tensor-core operator image (tensor form only)
+  __half* img = nullptr;           // tensor-core operator image (tensor form only)
+  float* op_scale = nullptr;       // its per-operator power-of-two scales
   double flops_rhs = 0;            // algorithmic flops per right-hand side
   double bytes_fixed = 0;          // operators (bytes once per launch)
   double bytes_rhs = 0;            // unique source rows + target rows (read and write), per rhs
@@ -110,7 +111,8 @@ struct Workspace {
   bool external = false;   // buffers carved from caller-provided memory
   DevArena ar;
   float2 *fs = nullptr, *us = nullptr, *p2m = nullptr, *p2l = nullptr;
-  float *ahi = nullptr, *alo = nullptr;                 // split source buffer (tensor form)
+  __half *ahi = nullptr, *alo = nullptr;                // split source buffer (tensor form)
+  float* ascale = nullptr;                              // its per-row scales
   std::vector<float2*> S, T;                            // per level (LF or HF states)
   std::vector<std::pair<void*, size_t>> zero;           // reset before each apply
   std::map<std::pair<const void*, int>, std::pair<int4*, int64_t>> tiles;   // key (stage, nrhs * 1024 + columns)
@@ -906,8 +908,21 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
 
 // ------------------------------------------------------------------- apply ---
 
+// Most rows of a translation stage's source buffer, per RHS.
+int64_t max_source_rows(const dfmm_plan_s* P) {
+  int64_t m = 1;
+  for (int l = 0; l < P->nl; ++l) {
+    if (l >= P->l_lf0) {
+      m = std::max({m, P->lf[l].nbox, P->lf[l].n_p2m, P->lf[l].n_p2l});
+    } else if (P->l_top >= 0 && l >= P->l_top) {
+      m = std::max(m, (int64_t)std::max(P->hf[l].out_keys.size(), P->hf[l].in_keys.size()));
+    }
+  }
+  return m;
+}
+
 // Largest source buffer of a translation stage, in complex elements per RHS
-// (the tensor form splits it into TF32 hi / lo float arrays).
+// (the tensor form splits it into FP16 hi / lo arrays).
 int64_t max_source_elems(const dfmm_plan_s* P) {
   int64_t m = 0;
   for (int l = 0; l < P->nl; ++l) {
@@ -961,8 +976,9 @@ Workspace* get_workspace(dfmm_plan_s* P, cudaStream_t s, int nrhs) {
   W->p2l = ar.alloc<float2>(p2l_rows * nrhs);
   if (P->opt.m2l_mode == 2) {
     int64_t e = max_source_elems(P) * nrhs * 2;
-    W->ahi = ar.alloc<float>(e);
-    W->alo = ar.alloc<float>(e);
+    W->ahi = ar.alloc<__half>(e);
+    W->alo = ar.alloc<__half>(e);
+    W->ascale = ar.alloc<float>(max_source_rows(P) * nrhs);
   }
   W->status = ar.alloc<unsigned>(1);
   W->zero.push_back({W->status, 4});   // reset by every apply; read by dfmm_sync_status
@@ -1018,8 +1034,8 @@ struct Runner {
     a.nrhs = nrhs;
     ProfScope ps(W, s, g.fam, g.flops_rhs * nrhs, g.bytes_fixed + g.bytes_rhs * nrhs);
     if (tc) {
-      launch_split(src, src_rows * nrhs, src_ld, W->ahi, W->alo, s);
-      TcArgs targs{g.img, W->ahi, W->alo};
+      launch_split(src, src_rows * nrhs, src_ld, W->ahi, W->alo, W->ascale, s);
+      TcArgs targs{g.img, g.op_scale, W->ahi, W->alo, W->ascale};
       launch_gemm_stage_tc(a, targs, W->status, s);
     } else {
       launch_gemm_stage(a, s);
@@ -1204,8 +1220,9 @@ void carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaStr
   W.p2l = (float2*)take(p2l_rows * nrhs * 8);
   if (P->opt.m2l_mode == 2) {
     size_t e = (size_t)max_source_elems(P) * nrhs * 2;
-    W.ahi = (float*)take(e * 4);
-    W.alo = (float*)take(e * 4);
+    W.ahi = (__half*)take(e * 2);
+    W.alo = (__half*)take(e * 2);
+    W.ascale = (float*)take((size_t)max_source_rows(P) * nrhs * 4);
   }
   W.status = (unsigned*)take(4);
   W.zero.push_back({W.status, 4});
@@ -1238,8 +1255,9 @@ void build_images(dfmm_plan_s* P, cudaStream_t s) {
   for (const GemmPlan* gc : all_gemms(P)) {
     GemmPlan* g = const_cast<GemmPlan*>(gc);
     if (g->npairs == 0 || g->nops == 0 || !gemm_tc_supported(g->M, g->Kd)) continue;
-    g->img = P->ar.alloc<float>(tc_image_floats(g->M, g->Kd, g->nops));
-    build_tc_image(g->ops, g->M, g->Kd, g->nops, g->img, s);
+    g->img = P->ar.alloc<__half>(tc_image_elems(g->M, g->Kd, g->nops));
+    g->op_scale = P->ar.alloc<float>(g->nops);
+    build_tc_image(g->ops, g->M, g->Kd, g->nops, g->img, g->op_scale, s);
   }
   DFMM_CUDA(cudaStreamSynchronize(s));
   P->stats.plan_bytes = (int64_t)P->ar.bytes();
@@ -1310,8 +1328,9 @@ int dfmm_plan(const double* points, int64_t N, double K, double eps, const dfmm_
     if (o.sketch_rows <= 0) o.sketch_rows = 400;
     if (!(o.eps_op_factor > 0)) o.eps_op_factor = 0.3;
     if (o.m2l_mode < 0 || o.m2l_mode > 2) return fail(DFMM_ERR_INVALID, "m2l_mode must be 0, 1 or 2");
-    // automatic form: split-TF32 tensor cores add about 3e-6 relative error,
-    // so they serve eps >= 1e-5; tighter tolerances use FP32 CUDA cores
+    // automatic form: the split-FP16 tensor-core form adds about 2e-6
+    // relative error, so it serves eps >= 1e-5; tighter tolerances use FP32
+    // CUDA cores
     if (o.m2l_mode == 0) o.m2l_mode = eps >= 1e-5 ? 2 : 1;
     P->opt = o;
     P->eps_op = eps * o.eps_op_factor;

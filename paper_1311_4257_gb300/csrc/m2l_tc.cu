@@ -3,34 +3,39 @@
 //
 // One CTA computes D = X Tb^T for one tile: 128 gathered source rows (pairs x
 // right-hand sides) against up to 256 real output components of one operator,
-// on the 5th-generation tensor cores (tcgen05.mma, kind::tf32, accumulators in
-// tensor memory).
+// on the 5th-generation tensor cores (tcgen05.mma, kind::f16 with FP32
+// accumulation in tensor memory).
 //
 //  * Complex arithmetic as a real GEMM: a state row is interleaved (re, im)
 //    floats, so with K = 2 R_s and N = 2 R_t the real-block operator
 //    Tb[2p][2q] = Re T, Tb[2p][2q+1] = -Im T, Tb[2p+1][2q] = Im T,
 //    Tb[2p+1][2q+1] = Re T maps a source row directly to an interleaved
 //    target row.
-//  * Split TF32: every operand x = hi + lo with hi = x rounded to TF32 and
-//    lo = (x - hi) rounded to TF32 (x is then represented to 2^-22 relative).
-//    The tensor core's FP32 accumulation does not round to nearest, so its
+//  * Scaled FP16 split: each source row x is scaled by a power of two
+//    s >= max |x| (exact), and x / s = hi + lo with hi = fp16(x / s) and
+//    lo = fp16(x / s - hi); each operator likewise with one power of two t.
+//    x is then represented to about 2^-22 of its row's largest entry (lo is
+//    subnormal only where that bound is absolute anyway).  The products
+//    hi hi, hi lo and lo hi are exact in FP32; the epilogue multiplies by s t.
+//  * The tensor core's FP32 accumulation does not round to nearest, so its
 //    error grows with the number of accumulation steps into one accumulator;
-//    the large term Ahi Bhi goes to one accumulator (one step per K = 8) and
-//    the small terms Ahi Blo + Alo Bhi to a second one, and the two are added
-//    in FP32 in the epilogue (Alo Blo, below 2^-22, is left out).
-//  * No conversion in the main loop: the operators are stored at plan time as
-//    an image of their shared-memory tiles (real-block form, TF32 hi and lo,
-//    canonical K-major layout without swizzle: 8-row x 16-byte core matrices,
-//    K-adjacent cores 128 B apart, 8-row groups 512 B apart), and the source
-//    states are split into hi / lo arrays by an elementwise pass before the
-//    stage.  Each stage's operator tile (hi and lo, contiguous in the image)
-//    arrives by one bulk copy (cp.async.bulk, completing on an mbarrier), the
-//    gathered state rows by 16-byte asynchronous copies (cp.async); 4 stages
-//    of 16 K-floats.
+//    the large term Ahi Bhi goes to one accumulator (one step per K = 16) and
+//    the small terms Ahi Blo + Alo Bhi to a second one, added in FP32 in the
+//    epilogue (Alo Blo, below 2^-22, is left out).
+//  * No conversion in the main loop: operators are stored at plan time as an
+//    image of their shared-memory tiles (real-block form, scaled FP16 hi and
+//    lo, canonical K-major layout without swizzle: 8-row x 16-byte core
+//    matrices, K-adjacent cores 128 B apart, 8-row groups 512 B apart; as
+//    many bytes as the complex64 operator), and the source states are split
+//    by a pass before the stage.  Each stage's operator tile arrives by one
+//    bulk copy (cp.async.bulk, completing on an mbarrier), the gathered state
+//    rows by 16-byte asynchronous copies (cp.async); 4 stages of 32 K-values.
 //  * One thread issues the MMAs and commits them to an mbarrier; stage reuse
 //    waits on it with a time limit.  The epilogue reads the accumulators with
 //    tcgen05.ld (row = gathered column) and scatter-adds them into the target
-//    states with float4 atomics.
+//    states with return-free vector reductions.
+#include <cuda_fp16.h>
+
 #include "apply.h"
 
 namespace dfmm {
@@ -38,23 +43,23 @@ namespace dfmm {
 namespace {
 
 constexpr int TC_M = 128;
-constexpr int TC_BK = 16;
+constexpr int TC_BK = 32;                          // K values (fp16) per stage
 constexpr int TC_NMAX = 256;
 constexpr int TC_THREADS = 256;
 constexpr int TC_STAGES = 4;
-constexpr int A_BYTES = TC_M * TC_BK * 4;          // 8 KB
-constexpr int B_BYTES = TC_NMAX * TC_BK * 4;       // 16 KB
+constexpr int A_BYTES = TC_M * TC_BK * 2;          // 8 KB
+constexpr int B_BYTES = TC_NMAX * TC_BK * 2;       // 16 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int SMEM_BYTES = TC_STAGES * STAGE_BYTES + 1024 + 128;
-constexpr int TMEM_COLS = 512;   // two accumulators of up to 256 columns
-constexpr int CORE_SBO = (TC_BK / 4) * 128;        // 512 B between 8-row groups
+constexpr int TMEM_COLS = 512;                     // two accumulators of up to 256 columns
+constexpr int CORE_SBO = (TC_BK / 8) * 128;        // 512 B between 8-row groups
 constexpr unsigned long long WAIT_NS = 200000000ull;    // 0.2 s bound on every wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// byte offset of element (row, k) in one stage tile (canonical K-major, no swizzle)
+// byte offset of fp16 element (row, k) in one stage tile (canonical K-major, no swizzle)
 __host__ __device__ __forceinline__ uint32_t kmaj_off(int row, int k) {
-  return (uint32_t)((row >> 3) * CORE_SBO + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+  return (uint32_t)((row >> 3) * CORE_SBO + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
 // shared-memory matrix descriptor: start, LBO = 128 B, SBO = 512 B,
@@ -67,9 +72,9 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
   return d;
 }
 
-// instruction descriptor, kind::tf32: D f32, A and B tf32, K-major, M = 128
-__device__ __forceinline__ uint32_t idesc_tf32(int n) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+// instruction descriptor, kind::f16: D f32, A and B f16, K-major, M = 128
+__device__ __forceinline__ uint32_t idesc_f16(int n) {
+  return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
 }
 
 __device__ __forceinline__ unsigned long long globaltimer() {
@@ -103,12 +108,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigne
   return true;
 }
 
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
 __device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
 }
@@ -134,9 +133,9 @@ __device__ __forceinline__ void red_add4(float* p, float a, float b, float c, fl
                : "memory");
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
           d_tmem),
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
@@ -153,13 +152,43 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// smallest power of two >= m (1 for m == 0)
+__device__ __forceinline__ float pow2_above(float m) {
+  if (!(m > 0.f)) return 1.f;
+  int e;
+  frexpf(m, &e);
+  return ldexpf(1.f, e);
+}
+
+__device__ __forceinline__ void split_h(float v, __half& h, __half& l) {
+  h = __float2half_rn(v);
+  l = __float2half_rn(v - __half2float(h));
+}
+
+// per-operator scale: power of two >= max |entry|
+__global__ void op_scale_kernel(const float2* __restrict__ ops, int64_t per_op, float* __restrict__ scale) {
+  __shared__ float red[256];
+  const float2* T = ops + (size_t)blockIdx.x * per_op;
+  float m = 0.f;
+  for (int64_t e = threadIdx.x; e < per_op; e += blockDim.x) m = fmaxf(m, fmaxf(fabsf(T[e].x), fabsf(T[e].y)));
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) scale[blockIdx.x] = pow2_above(red[0]);
+}
+
 // Operator image: for every (operator, N block b, K chunk c) two tiles (hi,
-// then lo) of rows_b x 16 floats in the stage layout,
-// rows_b = min(TC_NMAX, 2M - TC_NMAX b).
-__global__ void op_image_kernel(const float2* __restrict__ ops, int M, int Kd, int nops, float* __restrict__ img) {
-  const int nchunk = 2 * Kd / TC_BK;
+// then lo) of rows_b x 32 fp16 values in the stage layout,
+// rows_b = min(TC_NMAX, 2M - TC_NMAX b); values scaled by 1 / scale[op].
+__global__ void op_image_kernel(const float2* __restrict__ ops, const float* __restrict__ scale, int M, int Kd,
+                                int nops, __half* __restrict__ img) {
+  const int Kreal = 2 * Kd;
+  const int nchunk = (Kreal + TC_BK - 1) / TC_BK;
   const int nb = (2 * M + TC_NMAX - 1) / TC_NMAX;
-  const int64_t op_floats = (int64_t)2 * (2 * M) * (2 * Kd);
+  const int64_t op_elems = (int64_t)2 * (2 * M) * (nchunk * TC_BK);
   int64_t g = blockIdx.x;          // (op, b, c)
   const int c = (int)(g % nchunk);
   g /= nchunk;
@@ -167,35 +196,64 @@ __global__ void op_image_kernel(const float2* __restrict__ ops, int M, int Kd, i
   const int op = (int)(g / nb);
   if (op >= nops) return;
   const int rows = min(TC_NMAX, 2 * M - TC_NMAX * b);
-  float* hi = img + op * op_floats + (int64_t)b * nchunk * 2 * TC_NMAX * TC_BK + (int64_t)c * 2 * rows * TC_BK;
-  float* lo = hi + rows * TC_BK;
+  __half* hi = img + op * op_elems + (int64_t)b * nchunk * 2 * TC_NMAX * TC_BK + (int64_t)c * 2 * rows * TC_BK;
+  __half* lo = hi + rows * TC_BK;
   const float2* T = ops + (size_t)op * M * Kd;
+  const float inv = 1.f / scale[op];
   for (int e = threadIdx.x; e < rows * TC_BK; e += blockDim.x) {
     const int row = e / TC_BK, kk = e % TC_BK;
     const int j = TC_NMAX * b + row, k = c * TC_BK + kk;
-    const float2 tv = T[(size_t)(j >> 1) * Kd + (k >> 1)];
-    const int cj = j & 1, ck = k & 1;
-    const float v = (cj == ck) ? tv.x : (cj == 0 ? -tv.y : tv.y);
-    const float h = tf32_rna(v);
-    const uint32_t off = kmaj_off(row, kk) / 4;
+    float v = 0.f;
+    if (k < Kreal) {
+      const float2 tv = T[(size_t)(j >> 1) * Kd + (k >> 1)];
+      const int cj = j & 1, ck = k & 1;
+      v = ((cj == ck) ? tv.x : (cj == 0 ? -tv.y : tv.y)) * inv;
+    }
+    __half h, l;
+    split_h(v, h, l);
+    const uint32_t off = kmaj_off(row, kk) / 2;
     hi[off] = h;
-    lo[off] = tf32_rna(v - h);
+    lo[off] = l;
   }
 }
 
-__global__ void split_kernel(const float* __restrict__ x, int64_t n, float* __restrict__ hi, float* __restrict__ lo) {
-  int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
-  if (i >= n) return;
-  float4 v = *(const float4*)(x + i);
-  float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
-  float4 l = make_float4(tf32_rna(v.x - h.x), tf32_rna(v.y - h.y), tf32_rna(v.z - h.z), tf32_rna(v.w - h.w));
-  *(float4*)(hi + i) = h;
-  *(float4*)(lo + i) = l;
+// one warp per source row of len floats (a multiple of 16): scale and split
+__global__ void split_kernel(const float* __restrict__ x, int64_t rows, int len, __half* __restrict__ hi,
+                             __half* __restrict__ lo, float* __restrict__ scale) {
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  const float* xr = x + row * len;
+  float m = 0.f;
+  for (int k = lane * 4; k < len; k += 128) {
+    const float4 v = *(const float4*)(xr + k);
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const float s = pow2_above(m);
+  const float inv = 1.f / s;
+  if (lane == 0) scale[row] = s;
+  for (int k = lane * 4; k < len; k += 128) {
+    const float4 v = *(const float4*)(xr + k);
+    __half h0, h1, h2, h3, l0, l1, l2, l3;
+    split_h(v.x * inv, h0, l0);
+    split_h(v.y * inv, h1, l1);
+    split_h(v.z * inv, h2, l2);
+    split_h(v.w * inv, h3, l3);
+    __half2* ph = (__half2*)(hi + row * len + k);
+    __half2* pl = (__half2*)(lo + row * len + k);
+    ph[0] = __halves2half2(h0, h1);
+    ph[1] = __halves2half2(h2, h3);
+    pl[0] = __halves2half2(l0, l1);
+    pl[1] = __halves2half2(l2, l3);
+  }
 }
 
 __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcArgs t, unsigned* status) {
   extern __shared__ unsigned char smem_raw[];
   __shared__ int srcrow[TC_M];
+  __shared__ float colscale[TC_M];
   __shared__ float2* dstp[TC_M];
   __shared__ int s_ok;
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -209,20 +267,24 @@ __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcAr
   const int n0 = TC_NMAX * b;                        // first real output component
   const int n = min(TC_NMAX, 2 * a.M - n0);          // multiple of 16
   const int Kreal = 2 * a.Kd;                        // multiple of 16
-  const int nchunk = Kreal / TC_BK;
-  const int64_t op_floats = (int64_t)2 * (2 * a.M) * Kreal;
-  const float* img = t.img + tile.x * op_floats + (int64_t)b * nchunk * 2 * TC_NMAX * TC_BK;
+  const int nchunk = (Kreal + TC_BK - 1) / TC_BK;
+  const int64_t op_elems = (int64_t)2 * (2 * a.M) * (nchunk * TC_BK);
+  const __half* img = t.img + tile.x * op_elems + (int64_t)b * nchunk * 2 * TC_NMAX * TC_BK;
+  const float opscale = t.op_scale[tile.x];
 
   if (tid < TC_M) {
     int sr = -1;
+    float cs = 0.f;
     float2* dp = nullptr;
     if (tid < ncol) {
       const int p = tile.y + tid / a.nrhs, k = tid % a.nrhs;
       const int2 pr = a.pairs[p];
       sr = pr.x * a.nrhs + k;
+      cs = t.src_scale[sr] * opscale;
       dp = a.dst + ((int64_t)pr.y * a.nrhs + k) * a.dst_ld;
     }
     srcrow[tid] = sr;
+    colscale[tid] = cs;
     dstp[tid] = dp;
   }
   if (tid == 0) s_ok = (*(volatile unsigned*)status & kStatusTimeout) ? 0 : 1;
@@ -244,11 +306,11 @@ __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcAr
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const uint32_t idesc = idesc_tf32(n);
+  const uint32_t idesc = idesc_f16(n);
   const uint32_t sbase = smem_u32(smem);
 
-  // asynchronous copies of chunk c into its stage: A hi/lo (128 rows x 4
-  // pieces of 16 B each) and B hi/lo (n rows x 4 pieces, contiguous image)
+  // asynchronous copies of chunk c into its stage: A hi/lo (128 gathered rows
+  // x 4 pieces of 16 B) by all threads, the operator tile by one bulk copy
   auto issue = [&](int c) {
     const int st = c % TC_STAGES;
     const uint32_t sA = sbase + st * STAGE_BYTES;
@@ -257,13 +319,14 @@ __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcAr
     for (int e = tid; e < TC_M * 8; e += TC_THREADS) {
       const int row = e & (TC_M - 1), piece = (e >> 7) & 3, part = e >> 9;   // part 0 = hi, 1 = lo
       const int sr = srcrow[row];
-      const uint32_t dsts = sA + part * A_BYTES + kmaj_off(row, 4 * piece);
-      const float* base = part ? t.src_lo : t.src_hi;
-      if (sr >= 0) cp_async16(dsts, base + (int64_t)sr * Kreal + k0 + 4 * piece);
+      const int k = k0 + 8 * piece;
+      const uint32_t dsts = sA + part * A_BYTES + kmaj_off(row, 8 * piece);
+      const __half* base = part ? t.src_lo : t.src_hi;
+      if (sr >= 0 && k < Kreal) cp_async16(dsts, base + (int64_t)sr * Kreal + k);
       else cp_async16_zero(dsts, base);
     }
-    if (tid == 0) {   // operator tile: hi then lo, n x 16 floats each, one bulk copy
-      const uint32_t bytes = (uint32_t)(2 * n * TC_BK * 4);
+    if (tid == 0) {   // operator tile: hi then lo, n x 32 values each
+      const uint32_t bytes = (uint32_t)(2 * n * TC_BK * 2);
       mbar_expect_tx(smem_u32(&fullb[st]), bytes);
       bulk_g2s(sB, img + (int64_t)c * 2 * n * TC_BK, bytes, smem_u32(&fullb[st]));
     }
@@ -284,15 +347,15 @@ __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcAr
     if (!s_ok) break;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int ksteps = min(TC_BK, Kreal - c * TC_BK) / 16;
       const uint32_t ah = sbase + st * STAGE_BYTES, al = ah + A_BYTES, bh = al + A_BYTES;
-      const uint32_t bl = bh + (uint32_t)(n * TC_BK * 4);    // lo tile follows the hi tile
-#pragma unroll
-      for (int s = 0; s < TC_BK / 8; ++s) {
+      const uint32_t bl = bh + (uint32_t)(n * TC_BK * 2);    // lo tile follows the hi tile
+      for (int s = 0; s < ksteps; ++s) {
         const uint32_t off = 256u * s;
         const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
-        mma_tf32(tmem, smem_desc(ah + off), smem_desc(bh + off), idesc, acc);
-        mma_tf32(tmem + (uint32_t)TC_NMAX, smem_desc(ah + off), smem_desc(bl + off), idesc, acc);
-        mma_tf32(tmem + (uint32_t)TC_NMAX, smem_desc(al + off), smem_desc(bh + off), idesc, 1u);
+        mma_f16(tmem, smem_desc(ah + off), smem_desc(bh + off), idesc, acc);
+        mma_f16(tmem + 256u, smem_desc(ah + off), smem_desc(bl + off), idesc, acc);
+        mma_f16(tmem + 256u, smem_desc(al + off), smem_desc(bh + off), idesc, 1u);
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                        smem_u32(&bars[st]))
@@ -328,17 +391,19 @@ __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcAr
   // epilogue: accumulator lane 32 (warp % 4) + lane is gathered column c;
   // warps w and w + 4 share the lane quarter and split the 16-column chunks
   const int quarter = warp & 3, half = warp >> 2;
-  float2* dp = dstp[32 * quarter + lane];
+  const int col = 32 * quarter + lane;
+  float2* dp = dstp[col];
+  const float cs = colscale[col];
   for (int j0 = 16 * half; j0 < n; j0 += 32) {
     float v[16], w[16];
     tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)j0, v);
-    tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)TC_NMAX + (uint32_t)j0, w);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] += w[i];
+    tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + 256u + (uint32_t)j0, w);
     if (dp && ok) {
       float* out = (float*)dp + n0 + j0;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) red_add4(out + 4 * i, v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+      for (int q = 0; q < 4; ++q)
+        red_add4(out + 4 * q, (v[4 * q] + w[4 * q]) * cs, (v[4 * q + 1] + w[4 * q + 1]) * cs,
+                 (v[4 * q + 2] + w[4 * q + 2]) * cs, (v[4 * q + 3] + w[4 * q + 3]) * cs);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -352,22 +417,26 @@ int gemm_tc_columns() { return TC_M; }
 
 bool gemm_tc_supported(int M, int Kd) { return M % 8 == 0 && Kd % 8 == 0; }
 
-int64_t tc_image_floats(int M, int Kd, int nops) { return (int64_t)nops * 2 * (2 * M) * (2 * Kd); }
+int64_t tc_image_elems(int M, int Kd, int nops) {
+  const int nchunk = (2 * Kd + TC_BK - 1) / TC_BK;
+  return (int64_t)nops * 2 * (2 * M) * (nchunk * TC_BK);
+}
 
-void build_tc_image(const float2* ops, int M, int Kd, int nops, float* img, cudaStream_t s) {
+void build_tc_image(const float2* ops, int M, int Kd, int nops, __half* img, float* scale, cudaStream_t s) {
   if (nops == 0) return;
-  if (M % 8 != 0 || Kd % 8 != 0) throw Error(-5, "tensor-core stage needs ranks padded to a multiple of 8");
-  const int nchunk = 2 * Kd / TC_BK;
+  if (!gemm_tc_supported(M, Kd)) throw Error(-5, "tensor-core stage needs ranks padded to a multiple of 8");
+  op_scale_kernel<<<nops, 256, 0, s>>>(ops, (int64_t)M * Kd, scale);
+  const int nchunk = (2 * Kd + TC_BK - 1) / TC_BK;
   const int nb = (2 * M + TC_NMAX - 1) / TC_NMAX;
   int64_t blocks = (int64_t)nops * nb * nchunk;
-  op_image_kernel<<<(unsigned)blocks, 256, 0, s>>>(ops, M, Kd, nops, img);
+  op_image_kernel<<<(unsigned)blocks, 256, 0, s>>>(ops, scale, M, Kd, nops, img);
   DFMM_CUDA(cudaGetLastError());
 }
 
-void launch_split(const float2* x, int64_t rows, int ld, float* hi, float* lo, cudaStream_t s) {
-  int64_t n = rows * ld * 2;   // floats, a multiple of 16
-  if (n == 0) return;
-  split_kernel<<<(unsigned)((n / 4 + 255) / 256), 256, 0, s>>>((const float*)x, n, hi, lo);
+void launch_split(const float2* x, int64_t rows, int ld, __half* hi, __half* lo, float* scale, cudaStream_t s) {
+  if (rows == 0) return;
+  const int64_t threads = rows * 32;
+  split_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>((const float*)x, rows, 2 * ld, hi, lo, scale);
   DFMM_CUDA(cudaGetLastError());
 }
 
