@@ -137,58 +137,81 @@ __device__ __forceinline__ float2 green_phase(float phase, float inv_d) {
 
 constexpr int P2C_THREADS = 256;
 constexpr int P2C_CHUNK = 128;
-constexpr int P2C_RHS = 8;
+constexpr int P2C_JOBS = 8;   // rounds of side-by-side jobs per block
 
-__global__ __launch_bounds__(P2C_THREADS) void p2c_kernel(P2CArgs a) {
+// Check-point potentials of leaf points (the sample of Eq. 6 that P2M and P2L
+// project).  A group of tpj threads (one per check point) takes one job; a
+// block runs P2C_THREADS / tpj groups side by side, P2C_JOBS rounds in a row,
+// and keeps its check points in registers across the rounds.  NR right-hand
+// sides are accumulated per pass.
+template <int NR>
+__global__ __launch_bounds__(P2C_THREADS) void p2c_kernel(P2CArgs a, int tpj) {
   __shared__ float4 sp[P2C_CHUNK];
-  __shared__ float2 sf[P2C_CHUNK][P2C_RHS];
-  const int4 job = a.jobs[blockIdx.x];
-  const float4 sh = a.shifts[job.w];
-  for (int r0 = 0; r0 < a.nrhs; r0 += P2C_RHS) {
-    const int nr = min(P2C_RHS, a.nrhs - r0);
-    for (int p0 = 0; p0 < a.ld; p0 += P2C_THREADS) {
-      const int p = p0 + threadIdx.x;
-      ChkPt c = {};
-      if (p < a.nchk) c = a.chk[p];
-      float2 acc[P2C_RHS];
+  __shared__ float2 sf[P2C_CHUNK][NR];
+  const int jp = blockDim.x / tpj;
+  const int slice = P2C_CHUNK / jp;
+  const int grp = threadIdx.x / tpj, lane = threadIdx.x % tpj;
+  const int64_t jb0 = (int64_t)blockIdx.x * jp * P2C_JOBS;
+  const int64_t jb1 = min(a.njobs, jb0 + (int64_t)jp * P2C_JOBS);
+  for (int p0 = 0; p0 < a.nchk; p0 += tpj) {
+    const int p = p0 + lane;
+    ChkPt c = {};
+    if (p < a.nchk) c = a.chk[p];
+    for (int64_t jb = jb0; jb < jb1; jb += jp) {
+      const int64_t my = jb + grp;
+      const bool has = my < jb1;
+      const int4 job = has ? a.jobs[my] : make_int4(0, 0, 0, 0);
+      int maxy = 0;
+      for (int g = 0; g < jp && jb + g < jb1; ++g) maxy = max(maxy, a.jobs[jb + g].y);
+      const float4 sh = has ? a.shifts[job.w] : make_float4(0.f, 0.f, 0.f, 0.f);
+      float4* spg = sp + grp * slice;
+      float2(*sfg)[NR] = sf + grp * slice;
+      for (int r0 = 0; r0 < a.nrhs; r0 += NR) {
+        const int nr = min(NR, a.nrhs - r0);
+        float2 acc[NR];
 #pragma unroll
-      for (int k = 0; k < P2C_RHS; ++k) acc[k] = make_float2(0.f, 0.f);
-      for (int i0 = 0; i0 < job.y; i0 += P2C_CHUNK) {
-        const int ni = min(P2C_CHUNK, job.y - i0);
-        __syncthreads();
-        for (int e = threadIdx.x; e < ni; e += P2C_THREADS) {
-          float4 v = a.pts[job.x + i0 + e];
-          v.x += sh.x; v.y += sh.y; v.z += sh.z;
-          v.w = v.x * v.x + v.y * v.y + v.z * v.z;
-          sp[e] = v;
-        }
-        for (int e = threadIdx.x; e < ni * P2C_RHS; e += P2C_THREADS) {
-          int i = e / P2C_RHS, k = e % P2C_RHS;
-          sf[i][k] = k < nr ? a.fs[(int64_t)(job.x + i0 + i) * a.nrhs + r0 + k] : make_float2(0.f, 0.f);
-        }
-        __syncthreads();
-        if (p < a.nchk) {
-          for (int i = 0; i < ni; ++i) {
-            float4 v = sp[i];
-            // |x - v|^2 = |x|^2 + s,  s = |v|^2 - 2 x.v ; d - |x| = s / (d + |x|)
-            float s = fmaf(-2.f, c.x * v.x + c.y * v.y + c.z * v.z, v.w);
-            float d2 = c.nx2 + s;
-            float inv_d = rsqrtf(d2);
-            float d = d2 * inv_d;
-            float phase = c.fx + s / (d + c.nx);
-            float2 g = green_phase(phase, inv_d);
+        for (int k = 0; k < NR; ++k) acc[k] = make_float2(0.f, 0.f);
+        for (int i0 = 0; i0 < maxy; i0 += slice) {
+          const int ni = max(0, min(slice, job.y - i0));
+          __syncthreads();
+          for (int e = lane; e < ni; e += tpj) {
+            float4 v = a.pts[job.x + i0 + e];
+            v.x += sh.x; v.y += sh.y; v.z += sh.z;
+            v.w = v.x * v.x + v.y * v.y + v.z * v.z;
+            spg[e] = v;
+          }
+          for (int e = lane; e < ni * NR; e += tpj) {
+            int i = e / NR, k = e % NR;
+            sfg[i][k] = k < nr ? a.fs[(int64_t)(job.x + i0 + i) * a.nrhs + r0 + k] : make_float2(0.f, 0.f);
+          }
+          __syncthreads();
+          if (p < a.nchk) {
+            for (int i = 0; i < ni; ++i) {
+              float4 v = spg[i];
+              // |x - v|^2 = |x|^2 + s,  s = |v|^2 - 2 x.v ; d - |x| = s / (d + |x|)
+              float s = fmaf(-2.f, c.x * v.x + c.y * v.y + c.z * v.z, v.w);
+              float d2 = c.nx2 + s;
+              float inv_d = rsqrtf(d2);
+              float d = d2 * inv_d;
+              float phase = c.fx + s / (d + c.nx);
+              float2 g = green_phase(phase, inv_d);
 #pragma unroll
-            for (int k = 0; k < P2C_RHS; ++k) {
-              float2 f = sf[i][k];
-              acc[k].x = fmaf(g.x, f.x, fmaf(-g.y, f.y, acc[k].x));
-              acc[k].y = fmaf(g.x, f.y, fmaf(g.y, f.x, acc[k].y));
+              for (int k = 0; k < NR; ++k) {
+                float2 f = sfg[i][k];
+                acc[k].x = fmaf(g.x, f.x, fmaf(-g.y, f.y, acc[k].x));
+                acc[k].y = fmaf(g.x, f.y, fmaf(g.y, f.x, acc[k].y));
+              }
             }
           }
         }
-      }
-      if (p < a.ld) {
-        for (int k = 0; k < nr; ++k)
-          a.out[((int64_t)job.z * a.nrhs + r0 + k) * a.ld + p] = p < a.nchk ? acc[k] : make_float2(0.f, 0.f);
+        if (has) {
+          float2* out = a.out + (int64_t)job.z * a.nrhs * a.ld;
+          if (p < a.nchk)
+            for (int k = 0; k < nr; ++k) out[(int64_t)(r0 + k) * a.ld + p] = acc[k];
+          if (p0 == 0)   // zero padding rows of the check-point sample
+            for (int q = a.nchk + lane; q < a.ld; q += tpj)
+              for (int k = 0; k < nr; ++k) out[(int64_t)(r0 + k) * a.ld + q] = make_float2(0.f, 0.f);
+        }
       }
     }
   }
@@ -233,8 +256,8 @@ __global__ __launch_bounds__(256) void rows_kernel(RowsArgs a) {
 }
 
 constexpr int P2P_THREADS = 128;
-constexpr int P2P_CHUNK = 256;
-constexpr int P2P_RHS = 4;
+constexpr int P2P_CHUNK = 512;    // source points staged at a time
+constexpr int P2P_LEAVES = 64;    // U-list entries staged at a time
 
 // Exact sum a + b = s + e (Knuth's TwoSum; IEEE adds, no contraction).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
@@ -243,18 +266,29 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// Near field.  Coordinates are box-local double-floats (hi + lo), so the
-// difference of two nearby points keeps full single-precision relative
-// accuracy however close they are (the 1/d amplitude of the closest pairs
-// dominates their targets' potentials).  The leaf-centre shift is added
-// exactly with TwoSum when the source chunk is staged.
+// Near field (the U list of Sec. 2.4 and the HF near pairs of Sec. 3.2
+// evaluated directly, Eq. 1).  Coordinates are box-local double-floats
+// (hi + lo), so the difference of two nearby points keeps full single-precision
+// relative accuracy however close they are (the 1/d amplitude of the closest
+// pairs dominates their targets' potentials).  The leaf-centre shift is added
+// exactly with TwoSum when a source point is staged.  One block per target
+// leaf: up to P2P_LEAVES U-list entries are read at once and prefix-summed,
+// then their points are gathered into shared memory in parallel, P2P_CHUNK at
+// a time (each thread finds its point's leaf by binary search).  The threads
+// are split into groups that each take every ngrp-th staged source; NR
+// right-hand sides are accumulated per pass.
+template <int NR>
 __global__ __launch_bounds__(P2P_THREADS) void p2p_kernel(P2PArgs a) {
   __shared__ float4 syh[P2P_CHUNK];
   __shared__ float4 syl[P2P_CHUNK];
-  __shared__ float2 sf[P2P_CHUNK][P2P_RHS];
-  __shared__ float2 red[P2P_THREADS][P2P_RHS];
+  __shared__ float2 sf[P2P_CHUNK][NR];
+  __shared__ float2 red[P2P_THREADS][NR];
+  __shared__ int4 su[P2P_LEAVES];
+  __shared__ float4 ssh[P2P_LEAVES];
+  __shared__ int soff[P2P_LEAVES + 1];
   const int2 lr = a.leaf_range[blockIdx.x];
   const int64_t u0 = a.u_off[blockIdx.x], u1 = a.u_off[blockIdx.x + 1];
+  const int lane = threadIdx.x & 31;
   for (int t0 = 0; t0 < lr.y; t0 += P2P_THREADS) {
     const int nt = min(P2P_THREADS, lr.y - t0);
     const int ngrp = P2P_THREADS / nt;
@@ -262,33 +296,62 @@ __global__ __launch_bounds__(P2P_THREADS) void p2p_kernel(P2PArgs a) {
     const bool active = grp < ngrp;
     const float4 xh = a.pts[lr.x + t0 + ti];
     const float4 xl = a.pts_lo[lr.x + t0 + ti];
-    for (int r0 = 0; r0 < a.nrhs; r0 += P2P_RHS) {
-      const int nr = min(P2P_RHS, a.nrhs - r0);
-      float2 acc[P2P_RHS];
+    for (int r0 = 0; r0 < a.nrhs; r0 += NR) {
+      const int nr = min(NR, a.nrhs - r0);
+      float2 acc[NR];
 #pragma unroll
-      for (int k = 0; k < P2P_RHS; ++k) acc[k] = make_float2(0.f, 0.f);
-      for (int64_t u = u0; u < u1; ++u) {
-        const int4 src = a.u_src[u];
-        const float4 sh = a.shifts[src.z];
-        for (int j0 = 0; j0 < src.y; j0 += P2P_CHUNK) {
-          const int nj = min(P2P_CHUNK, src.y - j0);
-          __syncthreads();
-          for (int e = threadIdx.x; e < nj; e += P2P_THREADS) {
-            float4 vh = a.pts[src.x + j0 + e], vl = a.pts_lo[src.x + j0 + e];
+      for (int k = 0; k < NR; ++k) acc[k] = make_float2(0.f, 0.f);
+      for (int64_t ub = u0; ub < u1; ub += P2P_LEAVES) {
+        const int nb = (int)(u1 - ub < P2P_LEAVES ? u1 - ub : P2P_LEAVES);
+        __syncthreads();   // the previous batch has been consumed
+        if (threadIdx.x < nb) {
+          const int4 e = a.u_src[ub + threadIdx.x];
+          su[threadIdx.x] = e;
+          ssh[threadIdx.x] = a.shifts[e.z];
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {   // exclusive prefix of the leaf sizes
+          int v0 = lane < nb ? su[lane].y : 0;
+          int v1 = lane + 32 < nb ? su[lane + 32].y : 0;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, v0, o);
+            int w = __shfl_up_sync(0xffffffffu, v1, o);
+            if (lane >= o) { v0 += t; v1 += w; }
+          }
+          v1 += __shfl_sync(0xffffffffu, v0, 31);
+          soff[lane + 1] = v0;
+          soff[lane + 33] = v1;
+          if (lane == 0) soff[0] = 0;
+        }
+        __syncthreads();
+        const int total = soff[nb];
+        for (int c0 = 0; c0 < total; c0 += P2P_CHUNK) {
+          const int fill = min(P2P_CHUNK, total - c0);
+          if (c0 > 0) __syncthreads();
+          for (int e = threadIdx.x; e < fill; e += P2P_THREADS) {
+            const int q = c0 + e;
+            int lo = 0, hi = nb;   // soff[lo] <= q < soff[hi]
+            while (hi - lo > 1) {
+              const int mid = (lo + hi) >> 1;
+              if (soff[mid] <= q) lo = mid; else hi = mid;
+            }
+            const int j = su[lo].x + (q - soff[lo]);
+            const float4 sh = ssh[lo];
+            const float4 vh = a.pts[j], vl = a.pts_lo[j];
             float hx, hy, hz, ex, ey, ez;
             two_sum(vh.x, sh.x, hx, ex);
             two_sum(vh.y, sh.y, hy, ey);
             two_sum(vh.z, sh.z, hz, ez);
             syh[e] = make_float4(hx, hy, hz, 0.f);
             syl[e] = make_float4(vl.x + ex, vl.y + ey, vl.z + ez, 0.f);
-          }
-          for (int e = threadIdx.x; e < nj * P2P_RHS; e += P2P_THREADS) {
-            int j = e / P2P_RHS, k = e % P2P_RHS;
-            sf[j][k] = k < nr ? a.fs[(int64_t)(src.x + j0 + j) * a.nrhs + r0 + k] : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < NR; ++k)
+              sf[e][k] = k < nr ? a.fs[(int64_t)j * a.nrhs + r0 + k] : make_float2(0.f, 0.f);
           }
           __syncthreads();
           if (active) {
-            for (int j = grp; j < nj; j += ngrp) {
+            for (int j = grp; j < fill; j += ngrp) {
               const float4 yh = syh[j], yl = syl[j];
               float dx = (xh.x - yh.x) + (xl.x - yl.x);
               float dy = (xh.y - yh.y) + (xl.y - yl.y);
@@ -299,7 +362,7 @@ __global__ __launch_bounds__(P2P_THREADS) void p2p_kernel(P2PArgs a) {
                 inv_d = inv_d * fmaf(-0.5f * r2 * inv_d, inv_d, 1.5f);   // one Newton step
                 float2 g = green_phase(r2 * inv_d, inv_d);
 #pragma unroll
-                for (int k = 0; k < P2P_RHS; ++k) {
+                for (int k = 0; k < NR; ++k) {
                   float2 f = sf[j][k];
                   acc[k].x = fmaf(g.x, f.x, fmaf(-g.y, f.y, acc[k].x));
                   acc[k].y = fmaf(g.x, f.y, fmaf(g.y, f.x, acc[k].y));
@@ -311,19 +374,19 @@ __global__ __launch_bounds__(P2P_THREADS) void p2p_kernel(P2PArgs a) {
       }
       __syncthreads();
 #pragma unroll
-      for (int k = 0; k < P2P_RHS; ++k) red[threadIdx.x][k] = active ? acc[k] : make_float2(0.f, 0.f);
+      for (int k = 0; k < NR; ++k) red[threadIdx.x][k] = active ? acc[k] : make_float2(0.f, 0.f);
       __syncthreads();
       if (threadIdx.x < nt) {
         for (int k = 0; k < nr; ++k) {
-          float2 s = make_float2(0.f, 0.f);
+          float2 sum = make_float2(0.f, 0.f);
           for (int g = 0; g < ngrp; ++g) {
             float2 v = red[g * nt + threadIdx.x][k];
-            s.x += v.x;
-            s.y += v.y;
+            sum.x += v.x;
+            sum.y += v.y;
           }
-          float2* u = a.us + (int64_t)(lr.x + t0 + threadIdx.x) * a.nrhs + r0 + k;
-          float2 o = *u;
-          *u = make_float2(o.x + s.x, o.y + s.y);
+          float2* uu = a.us + (int64_t)(lr.x + t0 + threadIdx.x) * a.nrhs + r0 + k;
+          float2 o = *uu;
+          *uu = make_float2(o.x + sum.x, o.y + sum.y);
         }
       }
       __syncthreads();
@@ -354,7 +417,13 @@ void launch_permute_out(const float2* us, const int32_t* perm, int64_t N, int nr
 
 void launch_p2c(const P2CArgs& a, cudaStream_t s) {
   if (a.njobs == 0) return;
-  p2c_kernel<<<(unsigned)a.njobs, P2C_THREADS, 0, s>>>(a);
+  const int tpj = max(32, (min(a.nchk, P2C_THREADS) + 31) / 32 * 32);
+  const int jp = P2C_THREADS / tpj;
+  const unsigned grid = (unsigned)((a.njobs + (int64_t)jp * P2C_JOBS - 1) / ((int64_t)jp * P2C_JOBS));
+  if (a.nrhs == 1) p2c_kernel<1><<<grid, jp * tpj, 0, s>>>(a, tpj);
+  else if (a.nrhs == 2) p2c_kernel<2><<<grid, jp * tpj, 0, s>>>(a, tpj);
+  else if (a.nrhs <= 4) p2c_kernel<4><<<grid, jp * tpj, 0, s>>>(a, tpj);
+  else p2c_kernel<8><<<grid, jp * tpj, 0, s>>>(a, tpj);
   DFMM_CUDA(cudaGetLastError());
 }
 
@@ -367,7 +436,9 @@ void launch_rows(const RowsArgs& a, cudaStream_t s) {
 
 void launch_p2p(const P2PArgs& a, cudaStream_t s) {
   if (a.nleaves == 0) return;
-  p2p_kernel<<<(unsigned)a.nleaves, P2P_THREADS, 0, s>>>(a);
+  if (a.nrhs == 1) p2p_kernel<1><<<(unsigned)a.nleaves, P2P_THREADS, 0, s>>>(a);
+  else if (a.nrhs == 2) p2p_kernel<2><<<(unsigned)a.nleaves, P2P_THREADS, 0, s>>>(a);
+  else p2p_kernel<4><<<(unsigned)a.nleaves, P2P_THREADS, 0, s>>>(a);
   DFMM_CUDA(cudaGetLastError());
 }
 
