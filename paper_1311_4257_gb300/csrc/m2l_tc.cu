@@ -36,6 +36,8 @@
 //    states with return-free vector reductions.
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "apply.h"
 
 namespace dfmm {
@@ -45,12 +47,14 @@ namespace {
 constexpr int TC_M = 128;
 constexpr int TC_BK = 32;                          // K values (fp16) per stage
 constexpr int TC_NMAX = 256;
-constexpr int TC_THREADS = 256;
+constexpr int TC_PRODUCERS = 128;                 // warps 0-3: one gathered row each
+constexpr int TC_MMA_WARP = 8;                     // warps 4-7: epilogue; warp 8: MMA issuer
+constexpr int TC_THREADS = 288;
 constexpr int TC_STAGES = 4;
 constexpr int A_BYTES = TC_M * TC_BK * 2;          // 8 KB
 constexpr int B_BYTES = TC_NMAX * TC_BK * 2;       // 16 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int SMEM_BYTES = TC_STAGES * STAGE_BYTES + 1024 + 128;
+constexpr int SMEM_BYTES = TC_STAGES * STAGE_BYTES + 1024 + 256;
 constexpr int TMEM_COLS = 512;                     // two accumulators of up to 256 columns
 constexpr int CORE_SBO = (TC_BK / 8) * 128;        // 512 B between 8-row groups
 constexpr unsigned long long WAIT_NS = 200000000ull;    // 0.2 s bound on every wait
@@ -140,16 +144,25 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b,
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+// two 16-column loads (one per accumulator), one wait
+__device__ __forceinline__ void tmem_ld16_pair(uint32_t ta, uint32_t tb, float* v, float* w) {
+  uint32_t r[16], q[16];
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+      : "r"(ta));
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]),
+        "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15])
+      : "r"(tb));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 16; ++i) {
+    v[i] = __uint_as_float(r[i]);
+    w[i] = __uint_as_float(q[i]);
+  }
 }
 
 // smallest power of two >= m (1 for m == 0)
@@ -250,54 +263,59 @@ __global__ void split_kernel(const float* __restrict__ x, int64_t rows, int len,
   }
 }
 
-__global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcArgs t, unsigned* status) {
-  extern __shared__ unsigned char smem_raw[];
-  __shared__ int srcrow[TC_M];
-  __shared__ float colscale[TC_M];
-  __shared__ float2* dstp[TC_M];
-  __shared__ int s_ok;
-  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  uint64_t* bars = (uint64_t*)(smem + TC_STAGES * STAGE_BYTES);   // MMAs of a stage done
-  uint64_t* fullb = bars + TC_STAGES;                               // operator tile of a stage landed
-  uint32_t* tmem_slot = (uint32_t*)(fullb + TC_STAGES);
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int4 tile = a.tiles[blockIdx.x];
-  const int ncol = tile.z * a.nrhs;
-  const int b = blockIdx.y;
-  const int n0 = TC_NMAX * b;                        // first real output component
-  const int n = min(TC_NMAX, 2 * a.M - n0);          // multiple of 16
-  const int Kreal = 2 * a.Kd;                        // multiple of 16
-  const int nchunk = (Kreal + TC_BK - 1) / TC_BK;
-  const int64_t op_elems = (int64_t)2 * (2 * a.M) * (nchunk * TC_BK);
-  const __half* img = t.img + tile.x * op_elems + (int64_t)b * nchunk * 2 * TC_NMAX * TC_BK;
-  const float opscale = t.op_scale[tile.x];
+__device__ __forceinline__ void named_bar_producers() { asm volatile("bar.sync 1, %0;" ::"n"(TC_PRODUCERS) : "memory"); }
 
-  if (tid < TC_M) {
-    int sr = -1;
-    float cs = 0.f;
-    float2* dp = nullptr;
-    if (tid < ncol) {
-      const int p = tile.y + tid / a.nrhs, k = tid % a.nrhs;
-      const int2 pr = a.pairs[p];
-      sr = pr.x * a.nrhs + k;
-      cs = t.src_scale[sr] * opscale;
-      dp = a.dst + ((int64_t)pr.y * a.nrhs + k) * a.dst_ld;
-    }
-    srcrow[tid] = sr;
-    colscale[tid] = cs;
-    dstp[tid] = dp;
-  }
-  if (tid == 0) s_ok = (*(volatile unsigned*)status & kStatusTimeout) ? 0 : 1;
+// Wait without giving up early on another CTA's report (used only to let a
+// CTA's own copies and MMAs land before it frees its memory); time-limited.
+__device__ __forceinline__ bool mbar_wait_drain(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  unsigned long long t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity))
+    if (globaltimer() - t0 > WAIT_NS) return false;
+  return true;
+}
+
+// Persistent, warp-specialised stage kernel.  Work item = (tile, N block);
+// CTA x takes items x, x + gridDim.x, ...  Roles:
+//   warps 0-3  producers: thread r gathers gathered row r of each K chunk
+//              (cp.async, completion counted on the stage's full barrier),
+//              thread 0 also bulk-copies the operator tile; they run up to
+//              TC_STAGES chunks ahead, across items.
+//   warp 8     one thread issues the MMAs of a chunk once its stage is full,
+//              commits them to the stage's empty barrier, and after an
+//              item's last chunk to acc_full; it waits for acc_empty before
+//              it overwrites the accumulators with the next item.
+//   warps 4-7  epilogue: read the accumulators (warp 4 + q reads TMEM lanes
+//              32q..32q+31 = gathered columns), release them (acc_empty) and
+//              scatter-add into the target states.
+// Every wait is time-limited; on a timeout the CTA reports it, stops issuing,
+// lets its own copies and MMAs land, frees its tensor memory and returns.
+__global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcArgs t, int64_t nitems, int nb,
+                                                                unsigned* status) {
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ int s_start;
+  __shared__ int s_flag[2];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + TC_STAGES * STAGE_BYTES);
+  uint64_t* empty = full + TC_STAGES;
+  uint64_t* acc_full = empty + TC_STAGES;
+  uint64_t* acc_empty = acc_full + 1;
+  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) s_start = (*(volatile unsigned*)status & kStatusTimeout) ? 0 : 1;
   __syncthreads();
-  if (!s_ok) return;   // an earlier CTA gave up: skip the work, hold no tensor memory
+  if (!s_start) return;   // an earlier CTA gave up: skip the work, hold no tensor memory
   if (tid == 0) {
     for (int i = 0; i < TC_STAGES; ++i) {
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[i])));
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&fullb[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[i])), "n"(TC_PRODUCERS + 1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[i])));
     }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(acc_full)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(acc_empty)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == TC_MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                  "r"(TMEM_COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -306,109 +324,146 @@ __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcAr
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const uint32_t idesc = idesc_f16(n);
   const uint32_t sbase = smem_u32(smem);
+  const int Kreal = 2 * a.Kd;                        // multiple of 16
+  const int nchunk = (Kreal + TC_BK - 1) / TC_BK;
+  const int64_t op_elems = (int64_t)2 * (2 * a.M) * (nchunk * TC_BK);
 
-  // asynchronous copies of chunk c into its stage: A hi/lo (128 gathered rows
-  // x 4 pieces of 16 B) by all threads, the operator tile by one bulk copy
-  auto issue = [&](int c) {
-    const int st = c % TC_STAGES;
-    const uint32_t sA = sbase + st * STAGE_BYTES;
-    const uint32_t sB = sA + 2 * A_BYTES;
-    const int k0 = c * TC_BK;
-    for (int e = tid; e < TC_M * 8; e += TC_THREADS) {
-      const int row = e & (TC_M - 1), piece = (e >> 7) & 3, part = e >> 9;   // part 0 = hi, 1 = lo
-      const int sr = srcrow[row];
-      const int k = k0 + 8 * piece;
-      const uint32_t dsts = sA + part * A_BYTES + kmaj_off(row, 8 * piece);
-      const __half* base = part ? t.src_lo : t.src_hi;
-      if (sr >= 0 && k < Kreal) cp_async16(dsts, base + (int64_t)sr * Kreal + k);
-      else cp_async16_zero(dsts, base);
-    }
-    if (tid == 0) {   // operator tile: hi then lo, n x 32 values each
-      const uint32_t bytes = (uint32_t)(2 * n * TC_BK * 2);
-      mbar_expect_tx(smem_u32(&fullb[st]), bytes);
-      bulk_g2s(sB, img + (int64_t)c * 2 * n * TC_BK, bytes, smem_u32(&fullb[st]));
-    }
-  };
-
-  for (int c = 0; c < TC_STAGES - 1; ++c) {
-    if (c < nchunk) issue(c);
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  }
-  int issued = 0;
-  for (int c = 0; c < nchunk; ++c) {
-    const int st = c % TC_STAGES;
-    asm volatile("cp.async.wait_group %0;" ::"n"(TC_STAGES - 2) : "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) s_ok = mbar_wait(smem_u32(&fullb[st]), (c / TC_STAGES) & 1, status) ? 1 : 0;
-    __syncthreads();
-    if (!s_ok) break;
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const int ksteps = min(TC_BK, Kreal - c * TC_BK) / 16;
-      const uint32_t ah = sbase + st * STAGE_BYTES, al = ah + A_BYTES, bh = al + A_BYTES;
-      const uint32_t bl = bh + (uint32_t)(n * TC_BK * 2);    // lo tile follows the hi tile
-      for (int s = 0; s < ksteps; ++s) {
-        const uint32_t off = 256u * s;
-        const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
-        mma_f16(tmem, smem_desc(ah + off), smem_desc(bh + off), idesc, acc);
-        mma_f16(tmem + 256u, smem_desc(ah + off), smem_desc(bl + off), idesc, acc);
-        mma_f16(tmem + 256u, smem_desc(al + off), smem_desc(bh + off), idesc, 1u);
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&bars[st]))
-                   : "memory");
-    }
-    issued = c + 1;
-    // refill the stage of chunk c - 1 with chunk c + STAGES - 1 once its MMAs are done
-    const int cn = c + TC_STAGES - 1;
-    if (cn < nchunk) {
-      if (c >= 1) {
-        const int cp = c - 1;
-        if (tid == 0) s_ok = mbar_wait(smem_u32(&bars[cp % TC_STAGES]), (cp / TC_STAGES) & 1, status) ? 1 : 0;
-        __syncthreads();
-        if (!s_ok) break;
-      }
-      issue(cn);
-    }
-    asm volatile("cp.async.commit_group;" ::: "memory");
-  }
-  asm volatile("cp.async.wait_all;" ::: "memory");
-  // wait (bounded) for the last issued chunk: MMAs complete in order
-  if (tid == 0) {
-    int ok = s_ok;
-    if (issued > 0) {
-      const int last = issued - 1;
-      ok = mbar_wait(smem_u32(&bars[last % TC_STAGES]), (last / TC_STAGES) & 1, status) && ok;
-    }
-    s_ok = ok;
-  }
-  __syncthreads();
-  const bool ok = s_ok != 0 && issued == nchunk;
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  // epilogue: accumulator lane 32 (warp % 4) + lane is gathered column c;
-  // warps w and w + 4 share the lane quarter and split the 16-column chunks
-  const int quarter = warp & 3, half = warp >> 2;
-  const int col = 32 * quarter + lane;
-  float2* dp = dstp[col];
-  const float cs = colscale[col];
-  for (int j0 = 16 * half; j0 < n; j0 += 32) {
-    float v[16], w[16];
-    tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)j0, v);
-    tmem_ld16(tmem + ((uint32_t)(32 * quarter) << 16) + 256u + (uint32_t)j0, w);
-    if (dp && ok) {
-      float* out = (float*)dp + n0 + j0;
+  if (warp < TC_PRODUCERS / 32) {
+    // ---------------- producers ----------------
+    int64_t g = 0;   // chunks issued by this CTA
+    bool ok = true;
+    for (int64_t it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+      const int4 tile = a.tiles[it / nb];
+      const int b = (int)(it % nb);
+      const int n = min(TC_NMAX, 2 * a.M - TC_NMAX * b);
+      const __half* img = t.img + tile.x * op_elems + (int64_t)b * nchunk * 2 * TC_NMAX * TC_BK;
+      int64_t sr = -1;
+      if (tid < tile.z * a.nrhs) sr = (int64_t)a.pairs[tile.y + tid / a.nrhs].x * a.nrhs + tid % a.nrhs;
+      const __half* rh = t.src_hi + (sr < 0 ? 0 : sr) * Kreal;
+      const __half* rl = t.src_lo + (sr < 0 ? 0 : sr) * Kreal;
+      for (int c = 0; c < nchunk; ++c, ++g) {
+        const int st = (int)(g % TC_STAGES);
+        const int64_t j = g / TC_STAGES;
+        if (j > 0) {   // the stage's previous chunk has been consumed by the MMAs
+          if (tid == 0) s_flag[g & 1] = mbar_wait(smem_u32(&empty[st]), (uint32_t)((j - 1) & 1), status) ? 1 : 0;
+          named_bar_producers();
+          ok = s_flag[g & 1] != 0;
+          if (!ok) break;
+        }
+        const uint32_t sA = sbase + st * STAGE_BYTES;
+        const int k0 = c * TC_BK;
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
-        red_add4(out + 4 * q, (v[4 * q] + w[4 * q]) * cs, (v[4 * q + 1] + w[4 * q + 1]) * cs,
-                 (v[4 * q + 2] + w[4 * q + 2]) * cs, (v[4 * q + 3] + w[4 * q + 3]) * cs);
+        for (int piece = 0; piece < 4; ++piece) {
+          const int k = k0 + 8 * piece;
+          const uint32_t dh = sA + kmaj_off(tid, 8 * piece);
+          if (sr >= 0 && k < Kreal) {
+            cp_async16(dh, rh + k);
+            cp_async16(dh + A_BYTES, rl + k);
+          } else {
+            cp_async16_zero(dh, t.src_hi);
+            cp_async16_zero(dh + A_BYTES, t.src_lo);
+          }
+        }
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[st])) : "memory");
+        if (tid == 0) {   // operator tile: hi then lo, n x 32 values each
+          const uint32_t bytes = (uint32_t)(2 * n * TC_BK * 2);
+          mbar_expect_tx(smem_u32(&full[st]), bytes);
+          bulk_g2s(sA + 2 * A_BYTES, img + (int64_t)c * 2 * n * TC_BK, bytes, smem_u32(&full[st]));
+        }
+      }
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (tid == 0)   // the bulk copies of the last fills have landed
+      for (int64_t q = (g > TC_STAGES ? g - TC_STAGES : 0); q < g; ++q)
+        mbar_wait_drain(smem_u32(&full[q % TC_STAGES]), (uint32_t)((q / TC_STAGES) & 1));
+  } else if (warp == TC_MMA_WARP) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      int64_t g = 0, last = -1;
+      int i = 0;
+      bool ok = true;
+      for (int64_t it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++i) {
+        const int b = (int)(it % nb);
+        const int n = min(TC_NMAX, 2 * a.M - TC_NMAX * b);
+        const uint32_t idesc = idesc_f16(n);
+        if (i > 0 && !mbar_wait(smem_u32(acc_empty), (uint32_t)((i - 1) & 1), status)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int c = 0; c < nchunk; ++c, ++g) {
+          const int st = (int)(g % TC_STAGES);
+          if (!mbar_wait(smem_u32(&full[st]), (uint32_t)((g / TC_STAGES) & 1), status)) {
+            ok = false;
+            break;
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // cp.async data -> async proxy
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const int ksteps = min(TC_BK, Kreal - c * TC_BK) / 16;
+          const uint32_t ah = sbase + st * STAGE_BYTES, al = ah + A_BYTES, bh = al + A_BYTES;
+          const uint32_t bl = bh + (uint32_t)(n * TC_BK * 2);    // lo tile follows the hi tile
+          for (int s = 0; s < ksteps; ++s) {
+            const uint32_t off = 256u * s;
+            const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
+            mma_f16(tmem, smem_desc(ah + off), smem_desc(bh + off), idesc, acc);
+            mma_f16(tmem + 256u, smem_desc(ah + off), smem_desc(bl + off), idesc, acc);
+            mma_f16(tmem + 256u, smem_desc(al + off), smem_desc(bh + off), idesc, 1u);
+          }
+          asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                           smem_u32(&empty[st]))
+                       : "memory");
+          last = g;
+        }
+        if (!ok) break;
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(acc_full))
+                     : "memory");
+      }
+      // MMAs complete in order: once the last commit has arrived, all have
+      if (last >= 0) mbar_wait_drain(smem_u32(&empty[last % TC_STAGES]), (uint32_t)((last / TC_STAGES) & 1));
+    }
+    __syncwarp();
+  } else {
+    // ---------------- epilogue ----------------
+    const int quarter = warp & 3;
+    const int col = 32 * quarter + lane;
+    const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
+    int i = 0;
+    for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x, ++i) {
+      const int4 tile = a.tiles[it / nb];
+      const int b = (int)(it % nb);
+      const int n0 = TC_NMAX * b;
+      const int n = min(TC_NMAX, 2 * a.M - n0);
+      float* out = nullptr;
+      float cs = 0.f;
+      if (col < tile.z * a.nrhs) {
+        const int2 pr = a.pairs[tile.y + col / a.nrhs];
+        const int k = col % a.nrhs;
+        cs = t.src_scale[(int64_t)pr.x * a.nrhs + k] * t.op_scale[tile.x];
+        out = (float*)(a.dst + ((int64_t)pr.y * a.nrhs + k) * a.dst_ld) + n0;
+      }
+      int okw = 0;
+      if (lane == 0) okw = mbar_wait(smem_u32(acc_full), (uint32_t)(i & 1), status) ? 1 : 0;
+      okw = __shfl_sync(0xffffffffu, okw, 0);
+      if (!okw) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int j0 = 0; j0 < n; j0 += 16) {
+        float v[16], w[16];
+        tmem_ld16_pair(trow + (uint32_t)j0, trow + 256u + (uint32_t)j0, v, w);
+        if (out) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            red_add4(out + j0 + 4 * q, (v[4 * q] + w[4 * q]) * cs, (v[4 * q + 1] + w[4 * q + 1]) * cs,
+                     (v[4 * q + 2] + w[4 * q + 2]) * cs, (v[4 * q + 3] + w[4 * q + 3]) * cs);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(acc_empty)) : "memory");
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == TC_MMA_WARP) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
 }
 
 }  // namespace
@@ -444,13 +499,18 @@ void launch_gemm_stage_tc(const GemmArgs& a, const TcArgs& t, unsigned* status, 
   if (a.ntiles == 0) return;
   if (!gemm_tc_supported(a.M, a.Kd) || a.src_ld != a.Kd)
     throw Error(-5, "tensor-core stage needs ranks padded to a multiple of 8 and dense source rows");
-  static bool attr = false;
-  if (!attr) {
+  static int nsm[64] = {0};
+  int dev = 0;
+  DFMM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) throw Error(-1, "device ordinal out of range");
+  if (!nsm[dev]) {
     DFMM_CUDA(cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    attr = true;
+    DFMM_CUDA(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev));
   }
-  dim3 grid((unsigned)a.ntiles, (unsigned)((2 * a.M + TC_NMAX - 1) / TC_NMAX));
-  gemm_tc_kernel<<<grid, TC_THREADS, SMEM_BYTES, s>>>(a, t, status);
+  const int nb = (2 * a.M + TC_NMAX - 1) / TC_NMAX;
+  const int64_t nitems = a.ntiles * nb;
+  const unsigned grid = (unsigned)std::min<int64_t>(nitems, nsm[dev]);
+  gemm_tc_kernel<<<grid, TC_THREADS, SMEM_BYTES, s>>>(a, t, nitems, nb, status);
   DFMM_CUDA(cudaGetLastError());
 }
 
