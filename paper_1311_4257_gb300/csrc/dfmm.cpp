@@ -56,9 +56,9 @@ struct GemmPlan {
 };
 
 enum Fam { F_M2L_HF, F_M2L_LF, F_M2M, F_L2L, F_P2M_PROJ, F_P2L_PROJ, F_P2M_EVAL, F_P2L_EVAL, F_L2P, F_M2P, F_P2P,
-           F_PERMUTE, F_ZERO, F_COUNT };
+           F_PERMUTE, F_ZERO, F_SPLIT, F_COUNT };
 const char* kFamName[F_COUNT] = {"m2l_hf", "m2l_lf", "m2m", "l2l", "p2m_proj", "p2l_proj", "p2m_eval",
-                                 "p2l_eval", "l2p", "m2p", "p2p", "permute", "zero"};
+                                 "p2l_eval", "l2p", "m2p", "p2p", "permute", "zero", "split"};
 
 struct ProfRec {
   int fam;
@@ -1032,12 +1032,16 @@ struct Runner {
     a.src_ld = src_ld;
     a.dst_ld = dst_ld;
     a.nrhs = nrhs;
-    ProfScope ps(W, s, g.fam, g.flops_rhs * nrhs, g.bytes_fixed + g.bytes_rhs * nrhs);
     if (tc) {
-      launch_split(src, src_rows * nrhs, src_ld, W->ahi, W->alo, W->ascale, s);
+      {
+        ProfScope ps(W, s, F_SPLIT, 0.0, (double)src_rows * nrhs * src_ld * 16);
+        launch_split(src, src_rows * nrhs, src_ld, W->ahi, W->alo, W->ascale, s);
+      }
+      ProfScope ps(W, s, g.fam, g.flops_rhs * nrhs, g.bytes_fixed + g.bytes_rhs * nrhs);
       TcArgs targs{g.img, g.op_scale, W->ahi, W->alo, W->ascale};
       launch_gemm_stage_tc(a, targs, W->status, s);
     } else {
+      ProfScope ps(W, s, g.fam, g.flops_rhs * nrhs, g.bytes_fixed + g.bytes_rhs * nrhs);
       launch_gemm_stage(a, s);
     }
   }

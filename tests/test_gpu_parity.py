@@ -169,7 +169,7 @@ def test_config2_sphere_k64_sampled_targets():
 
 @pytest.mark.parametrize("nrhs", [1, 3])
 def test_tensor_core_form_matches_cuda_core_form(nrhs):
-    """The tcgen05 split-TF32 translations agree with the FP32 CUDA-core ones."""
+    """The tcgen05 scaled-FP16-split translations agree with the FP32 CUDA-core ones."""
     p = workloads.sphere(8.0, 0)
     f = workloads.densities(p.shape[0], nrhs, 3)
     u_tc = _apply(_plan(p, 8.0, 1e-5, m2l_mode=2), f)
