@@ -32,7 +32,16 @@ WORKLOADS = {
     "sphere_K8": dict(K=8.0, seed=0, eps=1e-6, desc="sphere diameter 8, N=20,106 (seed 0), eps 1e-6"),
     "sphere_K16": dict(K=16.0, seed=1, eps=1e-5, desc="sphere diameter 16, N=80,424 (seed 1), eps 1e-5"),
     "sphere_K32": dict(K=32.0, seed=1, eps=1e-5, desc="sphere diameter 32, N=321,699 (seed 1), eps 1e-5"),
+    "ellipsoid_K128": dict(K=128.0, seed=2, eps=1e-5, axes=(64.0, 32.0, 16.0),
+                           desc="ellipsoid semi-axes (64, 32, 16), K=128, N=1,625,002 (seed 2), eps 1e-5"),
 }
+
+
+def points_of(wl):
+    import workloads
+    if "axes" in wl:
+        return workloads.ellipsoid(*wl["axes"], seed=wl["seed"])
+    return workloads.sphere(wl["K"], wl["seed"])
 
 
 def peaks():
@@ -83,17 +92,17 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def traffic_for(kernel: str, source: str):
+def traffic_for(kernel: str, source: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source (null otherwise)."""
+    this workload with the current kernel source (null otherwise)."""
     src = open(os.path.join(ROOT, "paper_1311_4257_gb300", "csrc", source), "rb").read()
     h = hashlib.sha256(src).hexdigest()[:12]
     for fn in sorted(os.listdir(os.path.join(ROOT, "profiles"))) if os.path.isdir(os.path.join(ROOT, "profiles")) else []:
         if not fn.endswith(".md"):
             continue
         t = open(os.path.join(ROOT, "profiles", fn)).read()
-        m = re.search(r"traffic\[%s\]\s*=\s*([0-9.eE+]+)\s+bytes per launch\s+\(%s %s\)" % (
-            kernel, re.escape(source), h), t)
+        m = re.search(r"traffic\[%s @ %s\]\s*=\s*([0-9.eE+]+)\s+bytes per launch\s+\(%s %s\)" % (
+            kernel, re.escape(workload), re.escape(source), h), t)
         if m:
             return float(m.group(1))
     return None
@@ -117,7 +126,7 @@ def run_reference(args, wl):
     if rank != 0:
         return
     K = wl["K"]
-    p = workloads.sphere(K, wl["seed"])
+    p = points_of(wl)
     N = p.shape[0]
     f = workloads.densities(N, args.nrhs, wl["seed"])
     ntgt = args.ref_targets
@@ -159,7 +168,7 @@ def run_ours(args, wl):
         dist.init_process_group("nccl")
     B.build()
     K = wl["K"]
-    p = workloads.sphere(K, wl["seed"])
+    p = points_of(wl)
     N = p.shape[0]
     nrhs = args.nrhs
     f = workloads.densities(N, nrhs, wl["seed"])
@@ -249,8 +258,8 @@ def run_ours(args, wl):
                     "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["fp32_tflops"],
                     "peak_source": "FP32 CUDA-core peak 152 SM x 128 lanes x 2 x %.0f MHz (%s clock)" % (
                         pk["sm_max_mhz"], pk["source"])}
-    roofline.update({"traffic": traffic_for("gemm_tc_kernel", "m2l_tc.cu") if tc else
-                     traffic_for("gemm_stage_kernel", "apply.cu"),
+    roofline.update({"traffic": traffic_for("gemm_tc_kernel", "m2l_tc.cu", args.workload) if tc else
+                     traffic_for("gemm_stage_kernel", "apply.cu", args.workload),
                      "launches_per_step": launches / nprof, "ms_per_launch": g_ms / launches,
                      "flops_per_launch": g_flops / launches, "share_of_step": share})
     out = {"metric": METRIC, "value": value, "unit": "points*RHS/s", "n_gpus": world, "steps": args.steps,

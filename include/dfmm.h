@@ -128,8 +128,29 @@ typedef struct {
 
 int dfmm_plan_stats(dfmm_plan_t plan, dfmm_stats* out);
 
-/* Device bytes of the per-stream workspace that an apply with nrhs needs. */
+/* Device bytes of the workspace that one apply with nrhs right-hand sides
+ * needs (sorted densities and potentials, translation states, staging buffers
+ * and work tables; the plan itself is not included).  -1 on a bad argument. */
 int64_t dfmm_apply_workspace_bytes(dfmm_plan_t plan, int nrhs);
+
+/* Device bytes held by the plan (tree, lists, operators, evaluation rows);
+ * the same value as dfmm_stats.plan_bytes.  -1 for a NULL plan. */
+int64_t dfmm_plan_bytes(dfmm_plan_t plan);
+
+/* Several independent matvecs in one call: u[k] = G_k f[k] for k < count,
+ * where G_k is the operator of plans[k] (Eq. 1 on that plan's points) and
+ * f[k], u[k] are device pointers laid out as in dfmm_apply with nrhs[k]
+ * right-hand sides.  The paper treats one geometry at a time; this entry point
+ * batches uneven geometries so that their stages overlap on the device: the
+ * applies run on a library-owned pool of streams that wait for the work
+ * already queued on `stream`, and `stream` waits for all of them.  Asynchronous
+ * like dfmm_apply (no host sync); the caller keeps the buffers alive until
+ * the batch has finished on `stream`.  Errors: DFMM_ERR_INVALID for a NULL
+ * array or element, nrhs outside [1, 64], f[k] == u[k], or a plan of another
+ * device (nothing is launched then); a failure during launch returns its code
+ * and may leave earlier applies of the batch queued. */
+int dfmm_apply_batched(const dfmm_plan_t* plans, const void* const* f, void* const* u, const int* nrhs, int count,
+                       cudaStream_t stream);
 
 /* Export of the plan's tree and lists for parity tests (host buffers).
  * Call with a NULL buffer to get the required element count in *count.
@@ -173,6 +194,54 @@ int dfmm_apply_noalloc(dfmm_plan_t plan, const void* f, void* u, int nrhs, cudaS
 
 /* Size in bytes of the scratch array of dfmm_apply_noalloc. */
 int64_t dfmm_noalloc_capacity(void);
+
+/* Request server (the paper has no counterpart): continuous batching of
+ * matvec requests over plans that stay resident.
+ *
+ * dfmm_server_create starts a dispatcher thread that serves requests on
+ * `streams` streams of the current device.  It allocates one device arena of
+ * budget_bytes, and every running apply takes its staging buffers and
+ * workspace from that arena; nothing else is allocated while serving.
+ * Requests are admitted oldest first.  The dispatcher groups every pending
+ * request on the same plan, up to max_rhs right-hand sides in total, into one
+ * apply whose right-hand sides sit side by side.  A group starts when a
+ * stream is free and its footprint fits in the arena: 2 N nrhs complex64
+ * staging plus dfmm_apply_workspace_bytes.  Requests that arrive while others
+ * run are admitted as streams and memory free up.  A request that could never
+ * fit fails with DFMM_ERR_OOM.
+ *
+ * dfmm_server_submit queues one request: nrhs right-hand sides of the plan's
+ * N points, host buffers f_host (read) and u_host (written) of nrhs * N
+ * complex64 each, laid out as in dfmm_apply (pinned memory makes the copies
+ * asynchronous).  The caller keeps both buffers alive and untouched until
+ * dfmm_server_wait has returned for the ticket written to *ticket.
+ * dfmm_server_wait blocks until the request has finished or timeout_seconds
+ * have passed (DFMM_ERR_TIMEOUT; the ticket stays valid), then returns the
+ * request's status and, if latency_ms is not NULL, its submit-to-finish time.
+ * A ticket can be collected once.
+ * dfmm_server_destroy finishes every queued request, then frees the server. */
+typedef struct dfmm_server_s* dfmm_server_t;
+
+typedef struct {
+  int64_t requests_done;           /* finished without error */
+  int64_t requests_failed;
+  int64_t applies;                 /* grouped applies run */
+  int64_t rhs_done;                /* right-hand sides of the finished requests */
+  int64_t points_rhs_done;         /* sum over finished requests of N x nrhs */
+  int64_t pending;                 /* queued, not started */
+  int32_t max_concurrent_applies;  /* most groups running at once so far */
+  int32_t reserved;
+  double wall_seconds;             /* first submit to last finish */
+  double latency_p50_ms;           /* over finished requests */
+  double latency_p99_ms;
+} dfmm_server_report;
+
+int dfmm_server_create(int streams, int64_t budget_bytes, int max_rhs, dfmm_server_t* out);
+int dfmm_server_submit(dfmm_server_t server, dfmm_plan_t plan, const void* f_host, void* u_host, int nrhs,
+                       int64_t* ticket);
+int dfmm_server_wait(dfmm_server_t server, int64_t ticket, double timeout_seconds, double* latency_ms);
+int dfmm_server_stats(dfmm_server_t server, dfmm_server_report* out);
+int dfmm_server_destroy(dfmm_server_t server);
 
 /* Per-kernel timing of applies, measured with CUDA events that the library
  * records on the apply stream around each of its launches.

@@ -15,7 +15,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdfmm.so")
 
-SOURCES = ["sort.cu", "tree.cu", "operators.cu", "apply.cu", "m2l_tc.cu", "noalloc.cu", "skeleton.cpp", "dfmm.cpp"]
+SOURCES = ["sort.cu", "tree.cu", "operators.cu", "apply.cu", "m2l_tc.cu", "noalloc.cu", "skeleton.cpp", "dfmm.cpp",
+           "serve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

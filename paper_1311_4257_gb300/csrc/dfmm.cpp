@@ -1186,8 +1186,10 @@ std::vector<const GemmPlan*> all_gemms(dfmm_plan_s* P) {
 
 // Lays out the whole workspace of an apply with nrhs right-hand sides inside
 // [base, base + bytes): state buffers, staging buffers and the work tiles of
-// every stage (copied in on `s`).  No device memory is allocated.
-void carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaStream_t s, Workspace& W) {
+// every stage (copied in on `s`).  No device memory is allocated.  With
+// base == nullptr nothing is laid out or copied: the return value is the
+// number of bytes the layout needs.
+size_t carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaStream_t s, Workspace& W) {
   size_t off = 0;
   auto take = [&](size_t n) -> char* {
     off = (off + 255) & ~(size_t)255;
@@ -1244,6 +1246,7 @@ void carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaStr
   }
   std::vector<int4*> dst(tl.size());
   for (size_t k = 0; k < tl.size(); ++k) dst[k] = (int4*)take(tl[k].second.size() * sizeof(int4));
+  if (!base) return off;
   if (off > bytes)
     throw Error(DFMM_ERR_UNSUPPORTED, "apply needs " + std::to_string(off) + " bytes of scratch, more than the " +
                                           std::to_string(bytes) + " bytes of the static scratch array");
@@ -1252,6 +1255,13 @@ void carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaStr
                               cudaMemcpyHostToDevice, s));
     W.tiles[std::make_pair((const void*)tl[k].first, nrhs * 1024 + tl_cols[k])] = {dst[k], (int64_t)tl[k].second.size()};
   }
+  return off;
+}
+
+// Device bytes of one apply's workspace with nrhs right-hand sides.
+int64_t workspace_bytes(dfmm_plan_s* P, int nrhs) {
+  Workspace W;
+  return (int64_t)carve_workspace(P, nrhs, nullptr, 0, nullptr, W);
 }
 
 // Operator images of every translation stage for the tensor-core form.
@@ -1303,6 +1313,36 @@ int apply_with_scratch(dfmm_plan_s* P, const void* f, void* u, int nrhs, cudaStr
 }
 
 }  // namespace dfmm
+
+namespace {
+
+// Per-device pool of streams on which dfmm_apply_batched runs the geometries
+// of a batch side by side (created on first use, kept for the process).
+constexpr int kBatchStreams = 8;
+struct BatchStreams {
+  std::mutex mu;
+  cudaStream_t s[kBatchStreams] = {};
+  cudaEvent_t start = nullptr, done[kBatchStreams] = {};
+};
+
+BatchStreams& batch_streams(int dev) {
+  static std::mutex mu;
+  static std::map<int, std::unique_ptr<BatchStreams>> pools;
+  std::lock_guard<std::mutex> g(mu);
+  auto& slot = pools[dev];
+  if (!slot) {
+    std::unique_ptr<BatchStreams> B(new BatchStreams());
+    for (int j = 0; j < kBatchStreams; ++j) {
+      DFMM_CUDA(cudaStreamCreateWithFlags(&B->s[j], cudaStreamNonBlocking));
+      DFMM_CUDA(cudaEventCreateWithFlags(&B->done[j], cudaEventDisableTiming));
+    }
+    DFMM_CUDA(cudaEventCreateWithFlags(&B->start, cudaEventDisableTiming));
+    slot = std::move(B);
+  }
+  return *slot;
+}
+
+}  // namespace
 
 // --------------------------------------------------------------- C ABI ---
 
@@ -1413,14 +1453,46 @@ int dfmm_plan_stats(dfmm_plan_t plan, dfmm_stats* out) {
 }
 
 int64_t dfmm_apply_workspace_bytes(dfmm_plan_t plan, int nrhs) {
-  if (!plan || nrhs < 1) return -1;
-  int64_t b = 2 * plan->N * nrhs * 8;
-  for (int l = 0; l < plan->nl; ++l) {
-    if (l >= plan->l_lf0) b += 2 * plan->lf[l].nbox * nrhs * plan->lf[l].R * 8 + plan->lf[l].n_p2m * 2 * plan->lf[l].R * nrhs * 8;
-    else if (plan->l_top >= 0 && l >= plan->l_top)
-      b += ((int64_t)plan->hf[l].out_keys.size() + (int64_t)plan->hf[l].in_keys.size()) * nrhs * plan->hf[l].R * 8;
+  if (!plan || nrhs < 1 || nrhs > 64) return -1;
+  try {
+    return workspace_bytes(plan, nrhs);
+  } catch (...) {
+    return -1;
   }
-  return b;
+}
+
+int64_t dfmm_plan_bytes(dfmm_plan_t plan) { return plan ? plan->stats.plan_bytes : -1; }
+
+int dfmm_apply_batched(const dfmm_plan_t* plans, const void* const* f, void* const* u, const int* nrhs, int count,
+                       cudaStream_t stream) {
+  return guarded([&]() -> int {
+    if (count < 0) return fail(DFMM_ERR_INVALID, "count must be >= 0");
+    if (count == 0) return DFMM_OK;
+    if (!plans || !f || !u || !nrhs) return fail(DFMM_ERR_INVALID, "null argument");
+    int dev = -1;
+    DFMM_CUDA(cudaGetDevice(&dev));
+    for (int k = 0; k < count; ++k) {
+      if (!plans[k] || !f[k] || !u[k]) return fail(DFMM_ERR_INVALID, "null plan or buffer in the batch");
+      if (nrhs[k] < 1 || nrhs[k] > 64) return fail(DFMM_ERR_INVALID, "nrhs must be in [1, 64]");
+      if (f[k] == u[k]) return fail(DFMM_ERR_INVALID, "f and u must not alias");
+      if (plans[k]->device != dev) return fail(DFMM_ERR_INVALID, "a plan of the batch belongs to another device");
+    }
+    BatchStreams& B = batch_streams(dev);
+    std::lock_guard<std::mutex> g(B.mu);
+    // the batch starts after the work already queued on the caller's stream
+    DFMM_CUDA(cudaEventRecord(B.start, stream));
+    const int ns = std::min(count, kBatchStreams);
+    for (int j = 0; j < ns; ++j) DFMM_CUDA(cudaStreamWaitEvent(B.s[j], B.start, 0));
+    // geometries are independent: each runs its whole apply on one of the
+    // pool's streams, so their stages overlap on the device
+    for (int k = 0; k < count; ++k)
+      run_apply(plans[k], (const float2*)f[k], (float2*)u[k], nrhs[k], B.s[k % ns]);
+    for (int j = 0; j < ns; ++j) {
+      DFMM_CUDA(cudaEventRecord(B.done[j], B.s[j]));
+      DFMM_CUDA(cudaStreamWaitEvent(stream, B.done[j], 0));
+    }
+    return DFMM_OK;
+  });
 }
 
 int dfmm_export(dfmm_plan_t plan, int what, void* buffer, int64_t* count) {

@@ -54,6 +54,14 @@ class Stats(ctypes.Structure):
         return d
 
 
+class ServerReport(ctypes.Structure):
+    _fields_ = [("requests_done", ctypes.c_int64), ("requests_failed", ctypes.c_int64), ("applies", ctypes.c_int64),
+                ("rhs_done", ctypes.c_int64), ("points_rhs_done", ctypes.c_int64), ("pending", ctypes.c_int64),
+                ("max_concurrent_applies", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("wall_seconds", ctypes.c_double), ("latency_p50_ms", ctypes.c_double),
+                ("latency_p99_ms", ctypes.c_double)]
+
+
 class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
@@ -83,9 +91,20 @@ def lib() -> ctypes.CDLL:
         L.dfmm_apply_launches.argtypes = [vp, i32]
         L.dfmm_apply_launches.restype = i64
         L.dfmm_representation.argtypes = [dbl, i32, dbl, dbl, i32, i32, i32, ctypes.POINTER(i32), vp, vp, i32]
+        L.dfmm_plan_bytes.argtypes = [vp]
+        L.dfmm_plan_bytes.restype = i64
+        L.dfmm_apply_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                         ctypes.POINTER(i32), i32, vp]
+        L.dfmm_server_create.argtypes = [i32, i64, i32, ctypes.POINTER(vp)]
+        L.dfmm_server_submit.argtypes = [vp, vp, vp, vp, i32, ctypes.POINTER(i64)]
+        L.dfmm_server_wait.argtypes = [vp, i64, dbl, ctypes.POINTER(dbl)]
+        L.dfmm_server_stats.argtypes = [vp, ctypes.POINTER(ServerReport)]
+        L.dfmm_server_destroy.argtypes = [vp]
         L.dfmm_last_error.restype = ctypes.c_char_p
         for f in ("dfmm_plan", "dfmm_apply", "dfmm_apply_host", "dfmm_sync_status", "dfmm_destroy",
-                  "dfmm_plan_stats", "dfmm_export", "dfmm_representation", "dfmm_profile"):
+                  "dfmm_plan_stats", "dfmm_export", "dfmm_representation", "dfmm_profile", "dfmm_apply_batched",
+                  "dfmm_server_create", "dfmm_server_submit", "dfmm_server_wait", "dfmm_server_stats",
+                  "dfmm_server_destroy"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -190,6 +209,9 @@ class Plan:
     def workspace_bytes(self, nrhs: int) -> int:
         return int(lib().dfmm_apply_workspace_bytes(self._h, nrhs))
 
+    def plan_bytes(self) -> int:
+        return int(lib().dfmm_plan_bytes(self._h))
+
     def export(self, what) -> np.ndarray:
         wid = EXPORT[what] if isinstance(what, str) else int(what)
         n = ctypes.c_int64(0)
@@ -201,6 +223,67 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None):
             lib().dfmm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def apply_batched(plans, fs, us=None, stream=None):
+    """dfmm_apply_batched: u[k] = G_k f[k] for several plans in one call.
+    fs: cuda complex64 tensors [nrhs_k, N_k]; returns the list of u tensors."""
+    import torch
+    n = len(plans)
+    if len(fs) != n:
+        raise ValueError("one density tensor per plan")
+    fs = [f.reshape(1, -1) if f.ndim == 1 else f for f in fs]
+    for p, f in zip(plans, fs):
+        if f.dtype != torch.complex64 or not f.is_cuda or not f.is_contiguous() or f.shape[1] != p.N:
+            raise TypeError("each f must be a contiguous cuda complex64 [nrhs, N] tensor of its plan")
+    if us is None:
+        us = [torch.empty_like(f) for f in fs]
+    vp = ctypes.c_void_p
+    P = (vp * n)(*[p._h.value for p in plans])
+    F = (vp * n)(*[f.data_ptr() for f in fs])
+    U = (vp * n)(*[u.data_ptr() for u in us])
+    R = (ctypes.c_int * n)(*[int(f.shape[0]) for f in fs])
+    _check(lib().dfmm_apply_batched(P, F, U, R, n, _stream_ptr(stream)))
+    return us
+
+
+class Server:
+    """dfmm_server_*: continuous batching of matvec requests over resident plans.
+
+    submit() takes host complex64 buffers [nrhs, N] (pinned torch tensors keep
+    the copies asynchronous); the caller keeps them alive until wait() returns."""
+
+    def __init__(self, streams: int = 4, budget_bytes: int = 8 << 30, max_rhs: int = 16):
+        h = ctypes.c_void_p()
+        _check(lib().dfmm_server_create(streams, int(budget_bytes), max_rhs, ctypes.byref(h)))
+        self._h = h
+
+    def submit(self, plan: Plan, f_ptr: int, u_ptr: int, nrhs: int) -> int:
+        t = ctypes.c_int64(0)
+        _check(lib().dfmm_server_submit(self._h, plan._h, f_ptr, u_ptr, nrhs, ctypes.byref(t)))
+        return t.value
+
+    def wait(self, ticket: int, timeout: float = 60.0) -> float:
+        """Blocks until the request has finished; returns its latency in ms."""
+        lat = ctypes.c_double(0)
+        _check(lib().dfmm_server_wait(self._h, ticket, timeout, ctypes.byref(lat)))
+        return lat.value
+
+    def stats(self) -> dict:
+        r = ServerReport()
+        _check(lib().dfmm_server_stats(self._h, ctypes.byref(r)))
+        return {name: getattr(r, name) for name, _ in r._fields_ if name != "reserved"}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dfmm_server_destroy(self._h)
             self._h = None
 
     def __del__(self):

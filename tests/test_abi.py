@@ -42,6 +42,21 @@ def test_invalid_arguments_are_rejected_without_a_device(L):
     assert L.dfmm_plan(pts.ctypes.data, 4, -1.0, 1e-5, None, ctypes.byref(h)) == dfmm.ERR_UNSUPPORTED
     assert L.dfmm_apply(None, None, None, 1, None) == dfmm.ERR_INVALID
     assert b"null" in L.dfmm_last_error()
+    # batched apply: an empty batch is a no-op; missing arrays are rejected
+    assert L.dfmm_apply_batched(None, None, None, None, 0, None) == dfmm.OK
+    assert L.dfmm_apply_batched(None, None, None, None, 2, None) == dfmm.ERR_INVALID
+    assert L.dfmm_apply_batched(None, None, None, None, -1, None) == dfmm.ERR_INVALID
+    assert L.dfmm_plan_bytes(None) == -1
+    assert L.dfmm_apply_workspace_bytes(None, 1) == -1
+    # request server: argument checks come before any device call
+    assert L.dfmm_server_create(0, 1 << 20, 16, ctypes.byref(h)) == dfmm.ERR_INVALID
+    assert L.dfmm_server_create(4, 0, 16, ctypes.byref(h)) == dfmm.ERR_INVALID
+    assert L.dfmm_server_create(4, 1 << 20, 0, ctypes.byref(h)) == dfmm.ERR_INVALID
+    t = ctypes.c_int64(0)
+    assert L.dfmm_server_submit(None, None, None, None, 1, ctypes.byref(t)) == dfmm.ERR_INVALID
+    assert L.dfmm_server_wait(None, 1, 0.0, None) == dfmm.ERR_INVALID
+    assert L.dfmm_server_stats(None, None) == dfmm.ERR_INVALID
+    assert L.dfmm_server_destroy(None) == dfmm.OK
 
 
 @pytest.mark.parametrize("w,cell", [(1.0, 0), (0.5, -1)])

@@ -152,3 +152,53 @@ def make(name: str) -> tuple[np.ndarray, float]:
     if w["kind"] == "ellipsoid":
         return ellipsoid(*w["axes"], seed=w["seed"]), w["K"]
     raise KeyError(name)
+
+
+def batch_geometries() -> list[tuple[str, np.ndarray, float, int]]:
+    """Twelve geometries of uneven size for the batched form, seeds 10-21 in
+    this order: spheres K = 8/16/24/32/48; ellipsoids with semi-axes
+    (K/2, K/4, K/8) for K = 16/32/64; tori (R, R/4) for R = 8/16/24/32 with
+    K = 2.5 R.  Right-hand sides are assigned round-robin from (1, 4, 16, 32).
+    Returns (name, points, K, nrhs) tuples."""
+    out = []
+    seed = 10
+    for K in (8.0, 16.0, 24.0, 32.0, 48.0):
+        out.append((f"sphere_K{K:g}", sphere(K, seed), K))
+        seed += 1
+    for K in (16.0, 32.0, 64.0):
+        out.append((f"ellipsoid_K{K:g}", ellipsoid(K / 2, K / 4, K / 8, seed), K))
+        seed += 1
+    for R in (8.0, 16.0, 24.0, 32.0):
+        out.append((f"torus_R{R:g}", torus(R, seed), 2.5 * R))
+        seed += 1
+    rhs = (1, 4, 16, 32)
+    return [(name, p, K, rhs[k % 4]) for k, (name, p, K) in enumerate(out)]
+
+
+def served_geometries(scale: float = 1.0) -> list[tuple[str, np.ndarray, float]]:
+    """The eight resident plans of the served form (seeds 40-47): spheres
+    K = 16/32/64, ellipsoids (K/2, K/4, K/8) for K = 32/128, tori (R, R/4) for
+    R = 16/32 (K = 2.5 R) and a cube surface of edge 48.  `scale` < 1 shrinks
+    every size in wavelengths (for quick tests)."""
+    out = []
+    seed = 40
+    for K in (16.0, 32.0, 64.0):
+        out.append((f"sphere_K{K * scale:g}", sphere(K * scale, seed), K * scale))
+        seed += 1
+    for K in (32.0, 128.0):
+        k = K * scale
+        out.append((f"ellipsoid_K{k:g}", ellipsoid(k / 2, k / 4, k / 8, seed), k))
+        seed += 1
+    for R in (16.0, 32.0):
+        r = R * scale
+        out.append((f"torus_R{r:g}", torus(r, seed), 2.5 * r))
+        seed += 1
+    e = 48.0 * scale
+    out.append((f"cube_E{e:g}", cube_surface(e, seed), e))
+    return out
+
+
+def poisson_arrivals(n: int, rate_hz: float, seed: int) -> np.ndarray:
+    """Arrival times (s) of n requests of a Poisson stream."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_hz, n))
