@@ -318,21 +318,186 @@ def run_ours(args, wl):
         dist.destroy_process_group()
 
 
+def _plain_rate(plans_pts, cache_dir, max_cols: int = 4):
+    """Points x RHS per second of the plain form: FP32 CUDA-core plans, one
+    right-hand side per apply, one apply at a time, over each geometry (at
+    most max_cols columns each, so the comparison stays short)."""
+    import numpy as np
+    import torch
+    import workloads
+    from paper_1311_4257_gb300 import Plan
+    pts_rhs, secs = 0.0, 0.0
+    for p, K, eps, cols in plans_pts:
+        plain = Plan(p, K, eps, cache_dir=cache_dir, m2l_mode=1)
+        f1 = torch.as_tensor(workloads.densities(p.shape[0], 1, 77).astype(np.complex64), device="cuda")
+        plain.apply(f1)
+        torch.cuda.synchronize()
+        c = min(cols, max_cols)
+        t0 = time.perf_counter()
+        for _ in range(c):
+            plain.apply(f1)
+        torch.cuda.synchronize()
+        secs += time.perf_counter() - t0
+        pts_rhs += p.shape[0] * c
+        plain.close()
+    return pts_rhs / secs
+
+
+def run_batch12(args):
+    """The batched form: twelve geometries of uneven size and uneven RHS
+    counts in one dfmm_apply_batched call per step."""
+    import numpy as np
+    import torch
+    import workloads
+    from paper_1311_4257_gb300 import Plan, apply_batched
+    from paper_1311_4257_gb300 import build as B
+    from oracle import direct as OD
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    B.build()
+    geo = workloads.batch_geometries()
+    t0 = time.perf_counter()
+    plans = [Plan(p, K, 1e-5, cache_dir=args.cache_dir) for _, p, K, _ in geo]
+    plan_s = time.perf_counter() - t0
+    fs = [torch.as_tensor(workloads.densities(p.shape[0], r, 60 + k).astype(np.complex64), device="cuda")
+          for k, (_, p, _, r) in enumerate(geo)]
+    us = [torch.empty_like(f) for f in fs]
+    for _ in range(args.warmup):
+        apply_batched(plans, fs, us)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        apply_batched(plans, fs, us)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    work = sum(p.shape[0] * r for _, p, _, r in geo)
+    # the same work one geometry at a time (all its RHS in one apply)
+    e0.record()
+    for pl, f, u in zip(plans, fs, us):
+        pl.apply(f, u)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_seq = e0.elapsed_time(e1)
+    # accuracy: every geometry against the direct sum on 50 targets, first RHS
+    errs = {}
+    for (name, p, _, r), u, f in zip(geo, us, fs):
+        t = np.random.default_rng(5).choice(p.shape[0], 50, replace=False)
+        ud = OD.direct(p, f[:1].cpu().numpy().astype(np.complex128), t, chunk=8)
+        errs[name] = OD.rel_err(u[:1].cpu().numpy()[:, t].astype(np.complex128), ud)
+    plain = _plain_rate([(p, K, 1e-5, r) for _, p, K, r in geo], args.cache_dir) if args.compare else None
+    line = {"metric": METRIC, "value": work / (ms / 1e3), "unit": "points*RHS/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64 (fp32)", "data": "synthetic",
+            "config": {"workload": "batch of 12 geometries (spheres K=8..48, ellipsoids K=16..64, tori R=8..32; "
+                                   "seeds 10-21; nrhs 1/4/16/32 round-robin), eps 1e-5",
+                       "points": int(sum(p.shape[0] for _, p, _, _ in geo)), "points_x_rhs": int(work),
+                       "plan_seconds": plan_s},
+            "sequential_same_work_ms": ms_seq,
+            "plain_fp32_single_rhs_rate": plain,
+            "speedup_vs_plain": (work / (ms / 1e3)) / plain if plain else None,
+            "rel_err_vs_direct_sum_50_targets": errs}
+    print(json.dumps(line), flush=True)
+
+
+def run_served8(args):
+    """The served form: a Poisson request stream over eight resident plans,
+    served by the library's request server."""
+    import numpy as np
+    import torch
+    import workloads
+    from paper_1311_4257_gb300 import Plan, Server
+    from paper_1311_4257_gb300 import build as B
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    B.build()
+    geo = workloads.served_geometries()
+    t0 = time.perf_counter()
+    plans = [Plan(p, K, 1e-5, cache_dir=args.cache_dir) for _, p, K in geo]
+    plan_s = time.perf_counter() - t0
+    n = args.requests
+    rng = np.random.default_rng(30)
+    which = rng.integers(0, len(plans), n)
+    nrhs = rng.integers(1, 17, n)
+    arrive = workloads.poisson_arrivals(n, args.rate, 30)
+    # host buffers: one pinned density block of 16 RHS per plan, and a ring of
+    # 8 result buffers per plan (a request writes slot k mod 8)
+    fh = [torch.as_tensor(workloads.densities(pl.N, 16, 90 + k).astype(np.complex64)).pin_memory()
+          for k, pl in enumerate(plans)]
+    uh = [[torch.empty((16, pl.N), dtype=torch.complex64).pin_memory() for _ in range(8)] for pl in plans]
+    budget = int(args.budget_gb * (1 << 30))
+
+    def serve(times, count):
+        srv = Server(streams=4, budget_bytes=budget, max_rhs=16)
+        tick = []
+        start = time.perf_counter()
+        for k in range(count):
+            if times is not None:
+                dt = times[k] - (time.perf_counter() - start)
+                if dt > 0:
+                    time.sleep(dt)
+            w = int(which[k])
+            tick.append(srv.submit(plans[w], fh[w].data_ptr(), uh[w][k % 8].data_ptr(), int(nrhs[k])))
+        for t in tick:
+            srv.wait(t, timeout=600.0)
+        st = srv.stats()
+        srv.close()
+        return st
+
+    serve(arrive[:16] - arrive[0], 16)      # warm-up
+    st = serve(arrive, n)
+    sat = serve(None, n)                     # all requests at once: capacity
+    work = float(sum(plans[w].N * r for w, r in zip(which, nrhs)))
+    # the same stream at 60% of the measured capacity: latency without backlog
+    cap_rate = sat["points_rhs_done"] / sat["wall_seconds"] / (work / n)
+    light = serve(workloads.poisson_arrivals(n, 0.6 * cap_rate, 32), n)
+    plain = _plain_rate([(p, K, 1e-5, 16) for _, p, K in geo], args.cache_dir) if args.compare else None
+    line = {"metric": METRIC, "value": sat["points_rhs_done"] / sat["wall_seconds"], "unit": "points*RHS/s",
+            "n_gpus": 1, "steps": n, "warmup": 20, "ms_per_step": 1e3 * sat["wall_seconds"] / n,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32)",
+            "data": "synthetic",
+            "config": {"workload": "served: %d requests over 8 resident plans (spheres K=16/32/64, ellipsoids "
+                                   "K=32/128, tori R=16/32, cube edge 48; seeds 40-47), nrhs U{1..16}, eps 1e-5"
+                                   % n, "server": "4 streams, max 16 RHS per apply, %.0f GB arena" % args.budget_gb,
+                       "plan_seconds": plan_s, "points_x_rhs": work},
+            "poisson": {"rate_req_per_s": args.rate, "latency_p50_ms": st["latency_p50_ms"],
+                        "latency_p99_ms": st["latency_p99_ms"], "applies": st["applies"],
+                        "points_rhs_per_s": st["points_rhs_done"] / st["wall_seconds"],
+                        "max_concurrent_applies": st["max_concurrent_applies"]},
+            "saturated": {"latency_p50_ms": sat["latency_p50_ms"], "latency_p99_ms": sat["latency_p99_ms"],
+                          "applies": sat["applies"], "max_concurrent_applies": sat["max_concurrent_applies"]},
+            "poisson_at_60pct_capacity": {"rate_req_per_s": 0.6 * cap_rate, "latency_p50_ms": light["latency_p50_ms"],
+                                          "latency_p99_ms": light["latency_p99_ms"], "applies": light["applies"],
+                                          "points_rhs_per_s": light["points_rhs_done"] / light["wall_seconds"]},
+            "plain_fp32_single_rhs_rate": plain,
+            "speedup_vs_plain": (sat["points_rhs_done"] / sat["wall_seconds"]) / plain if plain else None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sphere_K64", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="sphere_K64", choices=sorted(WORKLOADS) + ["batch12", "served8"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--ref-targets", type=int, default=300)
     ap.add_argument("--cache-dir", default=os.path.join(tempfile.gettempdir(), "dfmm_cache"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", default="auto", choices=["auto", "fp32", "tc"])
     ap.add_argument("--compare", action="store_true", help="also time the plain FP32 form and 16 RHS")
+    ap.add_argument("--requests", type=int, default=600, help="served8: requests in the stream")
+    ap.add_argument("--rate", type=float, default=200.0, help="served8: Poisson arrival rate (1/s)")
+    ap.add_argument("--budget-gb", type=float, default=64.0, help="served8: the server's device arena")
     args = ap.parse_args()
     os.makedirs(args.cache_dir, exist_ok=True)
+    if args.workload in ("batch12", "served8"):
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the batched and served forms have no oracle "
+                              "timing; use a single-geometry workload"}), flush=True)
+        elif int(os.environ.get("RANK", "0")) == 0:
+            (run_batch12 if args.workload == "batch12" else run_served8)(args)
+        return
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":
         run_reference(args, wl)

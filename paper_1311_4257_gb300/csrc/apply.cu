@@ -351,22 +351,22 @@ __global__ __launch_bounds__(P2P_THREADS) void p2p_kernel(P2PArgs a) {
           }
           __syncthreads();
           if (active) {
+#pragma unroll 4
             for (int j = grp; j < fill; j += ngrp) {
               const float4 yh = syh[j], yl = syl[j];
               float dx = (xh.x - yh.x) + (xl.x - yl.x);
               float dy = (xh.y - yh.y) + (xl.y - yl.y);
               float dz = (xh.z - yh.z) + (xl.z - yl.z);
               float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-              if (r2 > 0.f) {
-                float inv_d = rsqrtf(r2);
-                inv_d = inv_d * fmaf(-0.5f * r2 * inv_d, inv_d, 1.5f);   // one Newton step
-                float2 g = green_phase(r2 * inv_d, inv_d);
+              // a coincident source (r2 == 0) contributes nothing: 1/d is set to 0
+              float inv_d = r2 > 0.f ? rsqrtf(r2) : 0.f;
+              inv_d = inv_d * fmaf(-0.5f * r2 * inv_d, inv_d, 1.5f);   // one Newton step
+              float2 g = green_phase(r2 * inv_d, inv_d);
 #pragma unroll
-                for (int k = 0; k < NR; ++k) {
-                  float2 f = sf[j][k];
-                  acc[k].x = fmaf(g.x, f.x, fmaf(-g.y, f.y, acc[k].x));
-                  acc[k].y = fmaf(g.x, f.y, fmaf(g.y, f.x, acc[k].y));
-                }
+              for (int k = 0; k < NR; ++k) {
+                float2 f = sf[j][k];
+                acc[k].x = fmaf(g.x, f.x, fmaf(-g.y, f.y, acc[k].x));
+                acc[k].y = fmaf(g.x, f.y, fmaf(g.y, f.x, acc[k].y));
               }
             }
           }

@@ -167,6 +167,20 @@ def test_config2_sphere_k64_sampled_targets():
     assert OD.rel_err(u[:, t], ud) <= 1e-5
 
 
+def test_config3_ellipsoid_k128_sampled_targets():
+    """Ellipsoid with semi-axes (64, 32, 16), K = 128, N = 1,625,002 (seed 2),
+    eps 1e-5, tensor-core form: 200 sampled targets against the direct sum of
+    Eq. 1, and the tensor-core result against the FP32 form on all targets."""
+    p = workloads.ellipsoid(64.0, 32.0, 16.0, 2)
+    assert p.shape[0] == 1625002
+    f = workloads.densities(p.shape[0], 1, 2)
+    u_tc = _apply(_plan(p, 128.0, 1e-5, m2l_mode=2), f)
+    t = np.random.default_rng(1002).choice(p.shape[0], 200, replace=False)
+    assert OD.rel_err(u_tc[:, t], OD.direct(p, f, t, chunk=8)) <= 1e-5
+    u_fp = _apply(_plan(p, 128.0, 1e-5, m2l_mode=1), f)
+    assert OD.rel_err(u_tc, u_fp) < 5e-6
+
+
 @pytest.mark.parametrize("nrhs", [1, 3])
 def test_tensor_core_form_matches_cuda_core_form(nrhs):
     """The tcgen05 scaled-FP16-split translations agree with the FP32 CUDA-core ones."""
