@@ -95,8 +95,11 @@ class Clocks:
 def traffic_for(kernel: str, source: str, workload: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on
     this workload with the current kernel source (null otherwise)."""
-    src = open(os.path.join(ROOT, "paper_1311_4257_gb300", "csrc", source), "rb").read()
-    h = hashlib.sha256(src).hexdigest()[:12]
+    # the kernel source and the plan builder (which fixes operators and tiles)
+    h = hashlib.sha256()
+    for name in source.split("+"):
+        h.update(open(os.path.join(ROOT, "paper_1311_4257_gb300", "csrc", name), "rb").read())
+    h = h.hexdigest()[:12]
     for fn in sorted(os.listdir(os.path.join(ROOT, "profiles"))) if os.path.isdir(os.path.join(ROOT, "profiles")) else []:
         if not fn.endswith(".md"):
             continue
@@ -258,8 +261,8 @@ def run_ours(args, wl):
                     "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["fp32_tflops"],
                     "peak_source": "FP32 CUDA-core peak 152 SM x 128 lanes x 2 x %.0f MHz (%s clock)" % (
                         pk["sm_max_mhz"], pk["source"])}
-    roofline.update({"traffic": traffic_for("gemm_tc_kernel", "m2l_tc.cu", args.workload) if tc else
-                     traffic_for("gemm_stage_kernel", "apply.cu", args.workload),
+    roofline.update({"traffic": traffic_for("gemm_tc_kernel", "m2l_tc.cu+dfmm.cpp", args.workload) if tc else
+                     traffic_for("gemm_stage_kernel", "apply.cu+dfmm.cpp", args.workload),
                      "launches_per_step": launches / nprof, "ms_per_launch": g_ms / launches,
                      "flops_per_launch": g_flops / launches, "share_of_step": share})
     out = {"metric": METRIC, "value": value, "unit": "points*RHS/s", "n_gpus": world, "steps": args.steps,

@@ -114,7 +114,7 @@ typedef struct {
   int64_t boxes[32];           /* non-empty boxes per level */
   int64_t leaves[32];          /* leaves per level */
   int64_t hf_pairs[32];        /* HF-M2L pairs per level */
-  int64_t hf_offsets[32];      /* distinct HF-M2L offsets (operators) per level */
+  int64_t hf_offsets[32];      /* distinct HF-M2L offsets per level */
   int64_t slots_out[32];       /* active outgoing (box, direction) per level */
   int64_t slots_in[32];        /* active incoming (box, direction) per level */
   int32_t rank[32];            /* padded representation rank per level */
@@ -124,6 +124,7 @@ typedef struct {
   double plan_seconds;         /* wall time of dfmm_plan */
   double m2l_flops;            /* algorithmic M2L flops per RHS: 8 r_t r_s per pair */
   double other_translation_flops; /* M2M, L2L, LF-M2L, P2M/L2P GEMMs per RHS */
+  int64_t hf_ops[32];          /* distinct HF-M2L operators per level (offsets up to cube symmetry) */
 } dfmm_stats;
 
 int dfmm_plan_stats(dfmm_plan_t plan, dfmm_stats* out);

@@ -19,6 +19,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <unordered_set>
 #include <string>
 #include <unordered_map>
 #include <vector>
@@ -195,6 +196,47 @@ double now() {
 }
 
 int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// The 48 signed permutations of the skeleton code as a group: inverse,
+// composition (mul[a][b] = a after b) and action on integer vectors, with
+// y_k = sign_k x_perm_k.
+struct SymTables {
+  int inv[48];
+  int mul[48][48];
+  int perm[48][3], sign[48][3];
+  void apply(int s, const int64_t* x, int64_t* y) const {
+    for (int k = 0; k < 3; ++k) y[k] = sign[s][k] * x[perm[s][k]];
+  }
+};
+
+const SymTables& sym_tables() {
+  static SymTables T = [] {
+    SymTables t;
+    const auto& syms = symmetries();
+    auto index_of = [&](const int* pm, const int* sg) {
+      for (int s = 0; s < 48; ++s) {
+        bool eq = true;
+        for (int k = 0; k < 3; ++k) eq = eq && syms[s].perm[k] == pm[k] && syms[s].sign[k] == sg[k];
+        if (eq) return s;
+      }
+      throw Error(DFMM_ERR_INVALID, "symmetry table is not closed");
+    };
+    for (int s = 0; s < 48; ++s)
+      for (int k = 0; k < 3; ++k) { t.perm[s][k] = syms[s].perm[k]; t.sign[s][k] = syms[s].sign[k]; }
+    for (int a = 0; a < 48; ++a) {
+      int pm[3], sg[3];
+      for (int k = 0; k < 3; ++k) { pm[t.perm[a][k]] = k; sg[t.perm[a][k]] = t.sign[a][k]; }
+      t.inv[a] = index_of(pm, sg);
+      for (int b = 0; b < 48; ++b) {
+        int pc[3], sc[3];
+        for (int k = 0; k < 3; ++k) { pc[k] = t.perm[b][t.perm[a][k]]; sc[k] = t.sign[a][k] * t.sign[b][t.perm[a][k]]; }
+        t.mul[a][b] = index_of(pc, sc);
+      }
+    }
+    return t;
+  }();
+  return T;
+}
 
 std::vector<int32_t> near_template(double w) {
   int R = (int)std::ceil(w) + 1;
@@ -626,15 +668,32 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
       const int R = H.R;
       std::vector<int32_t> op;
       std::vector<int2> pr;
-      // HF-M2L, one operator per offset m
+      // HF-M2L, one operator per offset m up to the cube's symmetries.  The
+      // skeleton of a cell is its orbit's canonical skeleton mapped by a
+      // signed permutation tau (points in the same order), and G depends only
+      // on distances, so the operator of (m, d_in, d_out) equals that of
+      // (tau_in^-1 m, canonical d_in, tau_in^-1 tau_out applied to the
+      // canonical d_out): pairs with equal keys share one operator exactly.
       {
         std::unordered_map<int64_t, int> offs;
+        std::unordered_set<int64_t> distinct_m;
         std::vector<OpSpec> specs;
         const PairList& Pp = H.pairs;
         int64_t Rm = 8 * (int64_t)std::ceil(H.w) + 8;
+        std::vector<int> canon, which;
+        canonical_cells(n_cells(H.w), canon, which);
+        const SymTables& ST = sym_tables();
         for (int64_t q = 0; q < Pp.n; ++q) {
           int64_t m0 = Pp.m[3 * q], m1 = Pp.m[3 * q + 1], m2 = Pp.m[3 * q + 2];
-          int64_t key = ((m0 + Rm) * (2 * Rm + 1) + (m1 + Rm)) * (2 * Rm + 1) + (m2 + Rm);
+          distinct_m.insert(((m0 + Rm) * (2 * Rm + 1) + (m1 + Rm)) * (2 * Rm + 1) + (m2 + Rm));
+          const int s_in = which[Pp.din[q]], s_out = which[Pp.dout[q]];
+          const int inv_in = ST.inv[s_in];
+          const int rho = ST.mul[inv_in][s_out];
+          int64_t mm[3];
+          const int64_t mv[3] = {m0, m1, m2};
+          ST.apply(inv_in, mv, mm);
+          int64_t key = ((mm[0] + Rm) * (2 * Rm + 1) + (mm[1] + Rm)) * (2 * Rm + 1) + (mm[2] + Rm);
+          key = ((key * 48 + rho) * 2048 + canon[Pp.din[q]]) * 2048 + canon[Pp.dout[q]];
           auto it = offs.find(key);
           int id;
           if (it == offs.end()) {
@@ -654,7 +713,8 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
         }
         m2l_flops += H.m2l.flops_rhs;
         H.m2l.fam = F_M2L_HF;
-        P->stats.hf_offsets[l] = (int64_t)specs.size();
+        P->stats.hf_offsets[l] = (int64_t)distinct_m.size();
+        P->stats.hf_ops[l] = (int64_t)specs.size();
         H.m2l.M = R; H.m2l.Kd = R; H.m2l.nops = (int)specs.size();
         if (!specs.empty()) {
           H.m2l.ops = ar.alloc<float2>((size_t)specs.size() * R * R);

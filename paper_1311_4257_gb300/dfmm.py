@@ -43,7 +43,7 @@ class Stats(ctypes.Structure):
                 ("rank", ctypes.c_int32 * 32), ("v_pairs", ctypes.c_int64), ("u_pairs", ctypes.c_int64),
                 ("w_pairs", ctypes.c_int64), ("x_pairs", ctypes.c_int64), ("p2p_interactions", ctypes.c_int64),
                 ("plan_bytes", ctypes.c_int64), ("plan_seconds", ctypes.c_double), ("m2l_flops", ctypes.c_double),
-                ("other_translation_flops", ctypes.c_double)]
+                ("other_translation_flops", ctypes.c_double), ("hf_ops", ctypes.c_int64 * 32)]
 
     def to_dict(self) -> dict:
         n = self.n_levels
