@@ -403,6 +403,37 @@ def run_batch12(args):
     print(json.dumps(line), flush=True)
 
 
+def run_solve(args):
+    """GMRES around the resident matvec: x + (4 / K) (a / 4 pi) G x = b on the
+    sphere K = 64 (a = area per point), to the plan's tolerance."""
+    import numpy as np
+    import torch
+    import workloads
+    from paper_1311_4257_gb300 import Plan
+    from paper_1311_4257_gb300 import build as B
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    B.build()
+    wl = WORKLOADS["sphere_K64"]
+    p = points_of(wl)
+    plan = Plan(p, wl["K"], wl["eps"], cache_dir=args.cache_dir)
+    b = torch.as_tensor(workloads.densities(p.shape[0], 1, 11)[0].astype(np.complex64), device="cuda")
+    # identity plus the single-layer sum scaled by 4 / K, so that |beta G| stays
+    # near 1 at every size (unscaled, (1/2) I + S stagnates at K = 64)
+    alpha, beta = 1.0, (1.0 / workloads.POINTS_PER_SQ_WAVELENGTH) / (4 * np.pi) * (4.0 / wl["K"])
+    plan.solve(b, alpha, beta, tol=1e-2)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x, it, rr = plan.solve(b, alpha, beta, tol=wl["eps"], restart=60, maxit=300)
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    line = {"metric": "GMRES solve of x + (4/K)(a/4pi) G x = b, seconds to rel. residual <= eps",
+            "value": sec, "unit": "s", "n_gpus": 1, "steps": 1, "warmup": 1, "ms_per_step": 1e3 * sec,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "c64 (fp32)",
+            "data": "synthetic", "config": {"workload": wl["desc"], "restart": 60},
+            "matvecs": it, "true_relative_residual": rr, "ms_per_iteration": 1e3 * sec / max(1, it + 1)}
+    print(json.dumps(line), flush=True)
+
+
 def run_served8(args):
     """The served form: a Poisson request stream over eight resident plans,
     served by the library's request server."""
@@ -482,7 +513,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sphere_K64", choices=sorted(WORKLOADS) + ["batch12", "served8"])
+    ap.add_argument("--workload", default="sphere_K64", choices=sorted(WORKLOADS) + ["batch12", "served8", "solve_K64"])
     ap.add_argument("--nrhs", type=int, default=1)
     ap.add_argument("--ref-targets", type=int, default=300)
     ap.add_argument("--cache-dir", default=os.path.join(tempfile.gettempdir(), "dfmm_cache"))
@@ -494,12 +525,12 @@ def main():
     ap.add_argument("--budget-gb", type=float, default=64.0, help="served8: the server's device arena")
     args = ap.parse_args()
     os.makedirs(args.cache_dir, exist_ok=True)
-    if args.workload in ("batch12", "served8"):
+    if args.workload in ("batch12", "served8", "solve_K64"):
         if args.impl == "reference":
-            print(json.dumps({"impl": "reference", "unavailable": "the batched and served forms have no oracle "
-                              "timing; use a single-geometry workload"}), flush=True)
+            print(json.dumps({"impl": "reference", "unavailable": "the batched, served and solve forms have no "
+                              "oracle timing; use a single-geometry workload"}), flush=True)
         elif int(os.environ.get("RANK", "0")) == 0:
-            (run_batch12 if args.workload == "batch12" else run_served8)(args)
+            {"batch12": run_batch12, "served8": run_served8, "solve_K64": run_solve}[args.workload](args)
         return
     wl = WORKLOADS[args.workload]
     if args.impl == "reference":

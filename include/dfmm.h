@@ -196,6 +196,24 @@ int dfmm_apply_noalloc(dfmm_plan_t plan, const void* f, void* u, int nrhs, cudaS
 /* Size in bytes of the scratch array of dfmm_apply_noalloc. */
 int64_t dfmm_noalloc_capacity(void);
 
+/* Iterative solution of (alpha I + beta G) x = b by restarted GMRES around the
+ * plan's matvec: the use the paper's fast matvec serves (Sec. 1: the
+ * discretised integral equation is solved by a Krylov method, one
+ * application of G per iteration).  b and x are device complex64 vectors of
+ * N values in the caller's point order; x holds the initial guess on entry
+ * and the solution on return.  alpha and beta are complex (re, im).  GMRES
+ * restarts every `restart` iterations (1..500) and stops once the estimated
+ * relative residual |b - A x| / |b| is <= tol or after maxit matvecs.  On
+ * return *iters (if not NULL) holds the number of matvecs of the Krylov
+ * iterations, and *relres (if not NULL) the true relative residual of x
+ * (one more matvec).  The accuracy of A is that of the plan (eps), so tol
+ * below about eps is not meaningful.  Allocates (restart + 2) N complex64 of
+ * device workspace per call; synchronises `stream` at every iteration (the
+ * small least-squares problem is solved on the host).  Returns DFMM_OK
+ * whether or not tol was reached (compare *relres), or an error status. */
+int dfmm_solve(dfmm_plan_t plan, double alpha_re, double alpha_im, double beta_re, double beta_im, const void* b,
+               void* x, int restart, int maxit, double tol, cudaStream_t stream, int* iters, double* relres);
+
 /* Request server (the paper has no counterpart): continuous batching of
  * matvec requests over plans that stay resident.
  *

@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdfmm.so")
 
 SOURCES = ["sort.cu", "tree.cu", "operators.cu", "apply.cu", "m2l_tc.cu", "noalloc.cu", "skeleton.cpp", "dfmm.cpp",
-           "serve.cpp"]
+           "serve.cpp", "solve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

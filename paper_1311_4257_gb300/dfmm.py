@@ -100,11 +100,13 @@ def lib() -> ctypes.CDLL:
         L.dfmm_server_wait.argtypes = [vp, i64, dbl, ctypes.POINTER(dbl)]
         L.dfmm_server_stats.argtypes = [vp, ctypes.POINTER(ServerReport)]
         L.dfmm_server_destroy.argtypes = [vp]
+        L.dfmm_solve.argtypes = [vp, dbl, dbl, dbl, dbl, vp, vp, i32, i32, dbl, vp, ctypes.POINTER(i32),
+                                 ctypes.POINTER(dbl)]
         L.dfmm_last_error.restype = ctypes.c_char_p
         for f in ("dfmm_plan", "dfmm_apply", "dfmm_apply_host", "dfmm_sync_status", "dfmm_destroy",
                   "dfmm_plan_stats", "dfmm_export", "dfmm_representation", "dfmm_profile", "dfmm_apply_batched",
                   "dfmm_server_create", "dfmm_server_submit", "dfmm_server_wait", "dfmm_server_stats",
-                  "dfmm_server_destroy"):
+                  "dfmm_server_destroy", "dfmm_solve"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -211,6 +213,22 @@ class Plan:
 
     def plan_bytes(self) -> int:
         return int(lib().dfmm_plan_bytes(self._h))
+
+    def solve(self, b, alpha=1.0, beta=1.0, x0=None, restart: int = 30, maxit: int = 300, tol: float = 1e-5,
+              stream=None):
+        """dfmm_solve: restarted GMRES for (alpha I + beta G) x = b.
+        b: cuda complex64 [N]; returns (x, matvecs, true relative residual)."""
+        import torch
+        if b.dtype != torch.complex64 or not b.is_cuda or b.numel() != self.N:
+            raise TypeError("b must be a cuda complex64 tensor of N values")
+        b = b.reshape(-1).contiguous()
+        x = torch.zeros_like(b) if x0 is None else x0.reshape(-1).clone()
+        a, c = complex(alpha), complex(beta)
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0)
+        _check(lib().dfmm_solve(self._h, a.real, a.imag, c.real, c.imag, b.data_ptr(), x.data_ptr(), restart, maxit,
+                                tol, _stream_ptr(stream), ctypes.byref(it), ctypes.byref(rr)))
+        return x, it.value, rr.value
 
     def export(self, what) -> np.ndarray:
         wid = EXPORT[what] if isinstance(what, str) else int(what)

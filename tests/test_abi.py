@@ -57,6 +57,10 @@ def test_invalid_arguments_are_rejected_without_a_device(L):
     assert L.dfmm_server_wait(None, 1, 0.0, None) == dfmm.ERR_INVALID
     assert L.dfmm_server_stats(None, None) == dfmm.ERR_INVALID
     assert L.dfmm_server_destroy(None) == dfmm.OK
+    # GMRES: argument checks come before any device call
+    it, rr = ctypes.c_int(0), ctypes.c_double(0)
+    assert L.dfmm_solve(None, 1.0, 0.0, 1.0, 0.0, None, None, 30, 100, 1e-5, None,
+                        ctypes.byref(it), ctypes.byref(rr)) == dfmm.ERR_INVALID
 
 
 @pytest.mark.parametrize("w,cell", [(1.0, 0), (0.5, -1)])
