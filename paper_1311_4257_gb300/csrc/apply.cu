@@ -193,7 +193,8 @@ __global__ __launch_bounds__(P2C_THREADS) void p2c_kernel(P2CArgs a, int tpj) {
               float d2 = c.nx2 + s;
               float inv_d = rsqrtf(d2);
               float d = d2 * inv_d;
-              float phase = c.fx + s / (d + c.nx);
+              // d + |x| >= |x| ~ w: the fast division's 2 ulp change the phase by < 1e-6 rad
+              float phase = c.fx + __fdividef(s, d + c.nx);
               float2 g = green_phase(phase, inv_d);
 #pragma unroll
               for (int k = 0; k < NR; ++k) {
@@ -358,9 +359,9 @@ __global__ __launch_bounds__(P2P_THREADS) void p2p_kernel(P2PArgs a) {
               float dy = (xh.y - yh.y) + (xl.y - yl.y);
               float dz = (xh.z - yh.z) + (xl.z - yl.z);
               float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-              // a coincident source (r2 == 0) contributes nothing: 1/d is set to 0
-              float inv_d = r2 > 0.f ? rsqrtf(r2) : 0.f;
-              inv_d = inv_d * fmaf(-0.5f * r2 * inv_d, inv_d, 1.5f);   // one Newton step
+              // a coincident source (r2 == 0) contributes nothing: 1/d is set to 0.
+              // rsqrtf's 2 ulp give |G| to 2e-7 and the phase to 1e-6 rad (d < 2).
+              const float inv_d = r2 > 0.f ? rsqrtf(r2) : 0.f;
               float2 g = green_phase(r2 * inv_d, inv_d);
 #pragma unroll
               for (int k = 0; k < NR; ++k) {
@@ -429,7 +430,7 @@ void launch_p2c(const P2CArgs& a, cudaStream_t s) {
 
 void launch_rows(const RowsArgs& a, cudaStream_t s) {
   if (a.njobs == 0) return;
-  if (a.R > 256) throw Error(-5, "representation rank above 256 is not supported");
+  if (a.R > 256 || a.R % 2) throw Error(-5, "representation rank must be even and at most 256");
   rows_kernel<<<(unsigned)a.njobs, 256, 0, s>>>(a);
   DFMM_CUDA(cudaGetLastError());
 }
