@@ -196,6 +196,22 @@ int dfmm_apply_noalloc(dfmm_plan_t plan, const void* f, void* u, int nrhs, cudaS
 /* Size in bytes of the scratch array of dfmm_apply_noalloc. */
 int64_t dfmm_noalloc_capacity(void);
 
+/* A captured apply (the paper has no counterpart): dfmm_graph_create lays out
+ * a workspace that the graph object owns (dfmm_apply_workspace_bytes of device
+ * memory), runs one ordinary apply of the plan on the device buffers f and u
+ * (nrhs right-hand sides, layout as in dfmm_apply) on `stream`, then captures
+ * the same apply into a CUDA graph.  dfmm_graph_launch replays it on any
+ * stream of the device: u = G f with the contents f has when the replay runs,
+ * as one graph launch instead of some thirty kernel launches and memsets.  f
+ * and u must stay allocated while the graph exists; concurrent replays of one
+ * graph must not overlap (they share the workspace).  dfmm_graph_destroy waits
+ * for the device, then frees the graph and its workspace.  Errors: as
+ * dfmm_apply; DFMM_ERR_CUDA if the capture fails. */
+typedef struct dfmm_graph_s* dfmm_graph_t;
+int dfmm_graph_create(dfmm_plan_t plan, const void* f, void* u, int nrhs, cudaStream_t stream, dfmm_graph_t* out);
+int dfmm_graph_launch(dfmm_graph_t graph, cudaStream_t stream);
+int dfmm_graph_destroy(dfmm_graph_t graph);
+
 /* Iterative solution of (alpha I + beta G) x = b by restarted GMRES around the
  * plan's matvec: the use the paper's fast matvec serves (Sec. 1: the
  * discretised integral equation is solved by a Krylov method, one

@@ -189,6 +189,22 @@ struct dfmm_plan_s {
   std::map<cudaStream_t, std::unique_ptr<Workspace>> ws;
 };
 
+// A captured apply: the CUDA graph of run_apply on fixed buffers, with its own
+// workspace (laid out once, reused by every launch).
+struct dfmm_graph_s {
+  dfmm_plan_s* plan = nullptr;
+  DevArena ar;
+  char* scratch = nullptr;
+  size_t bytes = 0;
+  Workspace W;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~dfmm_graph_s() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+
 namespace {
 
 double now() {
@@ -1522,6 +1538,59 @@ int64_t dfmm_apply_workspace_bytes(dfmm_plan_t plan, int nrhs) {
 }
 
 int64_t dfmm_plan_bytes(dfmm_plan_t plan) { return plan ? plan->stats.plan_bytes : -1; }
+
+int dfmm_graph_create(dfmm_plan_t plan, const void* f, void* u, int nrhs, cudaStream_t stream, dfmm_graph_t* out) {
+  return guarded([&]() -> int {
+    if (!out) return fail(DFMM_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!plan || !f || !u) return fail(DFMM_ERR_INVALID, "null argument");
+    if (nrhs < 1 || nrhs > 64) return fail(DFMM_ERR_INVALID, "nrhs must be in [1, 64]");
+    if (f == u) return fail(DFMM_ERR_INVALID, "f and u must not alias");
+    int dev = -1;
+    DFMM_CUDA(cudaGetDevice(&dev));
+    if (dev != plan->device) return fail(DFMM_ERR_INVALID, "the plan belongs to another device");
+    std::unique_ptr<dfmm_graph_s> G(new dfmm_graph_s());
+    G->bytes = (size_t)workspace_bytes(plan, nrhs);
+    G->scratch = G->ar.alloc<char>(G->bytes);
+    // work tables are copied in here, outside the capture
+    carve_workspace(plan, nrhs, G->scratch, G->bytes, stream, G->W);
+    // one ordinary run first: initialises per-kernel launch attributes
+    run_apply(plan, (const float2*)f, (float2*)u, nrhs, stream, nullptr, &G->W);
+    DFMM_CUDA(cudaStreamSynchronize(stream));
+    cudaStream_t cs;
+    DFMM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    struct SG { cudaStream_t s; ~SG() { cudaStreamDestroy(s); } } sg{cs};
+    DFMM_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    try {
+      run_apply(plan, (const float2*)f, (float2*)u, nrhs, cs, nullptr, &G->W);
+    } catch (...) {
+      cudaGraph_t g = nullptr;
+      cudaStreamEndCapture(cs, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    DFMM_CUDA(cudaStreamEndCapture(cs, &G->graph));
+    DFMM_CUDA(cudaGraphInstantiate(&G->exec, G->graph, 0));
+    G->plan = plan;
+    *out = G.release();
+    return DFMM_OK;
+  });
+}
+
+int dfmm_graph_launch(dfmm_graph_t graph, cudaStream_t stream) {
+  return guarded([&]() -> int {
+    if (!graph) return fail(DFMM_ERR_INVALID, "null graph");
+    DFMM_CUDA(cudaGraphLaunch(graph->exec, stream));
+    return DFMM_OK;
+  });
+}
+
+int dfmm_graph_destroy(dfmm_graph_t graph) {
+  if (!graph) return DFMM_OK;
+  cudaDeviceSynchronize();
+  delete graph;
+  return DFMM_OK;
+}
 
 int dfmm_apply_batched(const dfmm_plan_t* plans, const void* const* f, void* const* u, const int* nrhs, int count,
                        cudaStream_t stream) {

@@ -100,13 +100,17 @@ def lib() -> ctypes.CDLL:
         L.dfmm_server_wait.argtypes = [vp, i64, dbl, ctypes.POINTER(dbl)]
         L.dfmm_server_stats.argtypes = [vp, ctypes.POINTER(ServerReport)]
         L.dfmm_server_destroy.argtypes = [vp]
+        L.dfmm_graph_create.argtypes = [vp, vp, vp, i32, vp, ctypes.POINTER(vp)]
+        L.dfmm_graph_launch.argtypes = [vp, vp]
+        L.dfmm_graph_destroy.argtypes = [vp]
         L.dfmm_solve.argtypes = [vp, dbl, dbl, dbl, dbl, vp, vp, i32, i32, dbl, vp, ctypes.POINTER(i32),
                                  ctypes.POINTER(dbl)]
         L.dfmm_last_error.restype = ctypes.c_char_p
         for f in ("dfmm_plan", "dfmm_apply", "dfmm_apply_host", "dfmm_sync_status", "dfmm_destroy",
                   "dfmm_plan_stats", "dfmm_export", "dfmm_representation", "dfmm_profile", "dfmm_apply_batched",
                   "dfmm_server_create", "dfmm_server_submit", "dfmm_server_wait", "dfmm_server_stats",
-                  "dfmm_server_destroy", "dfmm_solve"):
+                  "dfmm_server_destroy", "dfmm_solve", "dfmm_graph_create", "dfmm_graph_launch",
+                  "dfmm_graph_destroy"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -214,6 +218,19 @@ class Plan:
     def plan_bytes(self) -> int:
         return int(lib().dfmm_plan_bytes(self._h))
 
+    def graph(self, f, u, stream=None) -> "Graph":
+        """dfmm_graph_create: capture the apply u = G f on these buffers."""
+        import torch
+        f2 = f.reshape(1, -1) if f.ndim == 1 else f
+        if f2.dtype != torch.complex64 or not f2.is_cuda or not f2.is_contiguous() or f2.shape[1] != self.N:
+            raise TypeError("f must be a contiguous cuda complex64 [nrhs, N] tensor")
+        if u.shape != f.shape or u.dtype != f.dtype or not u.is_contiguous():
+            raise TypeError("u must match f")
+        h = ctypes.c_void_p()
+        _check(lib().dfmm_graph_create(self._h, f2.data_ptr(), u.data_ptr(), int(f2.shape[0]), _stream_ptr(stream),
+                                       ctypes.byref(h)))
+        return Graph(h, self, f, u)
+
     def solve(self, b, alpha=1.0, beta=1.0, x0=None, restart: int = 30, maxit: int = 300, tol: float = 1e-5,
               stream=None):
         """dfmm_solve: restarted GMRES for (alpha I + beta G) x = b.
@@ -241,6 +258,29 @@ class Plan:
     def close(self):
         if getattr(self, "_h", None):
             lib().dfmm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Graph:
+    """A captured apply (dfmm_graph_*): launch() recomputes u = G f from the
+    current contents of the f tensor it was created with."""
+
+    def __init__(self, h, plan, f, u):
+        self._h, self.plan, self.f, self.u = h, plan, f, u
+
+    def launch(self, stream=None):
+        _check(lib().dfmm_graph_launch(self._h, _stream_ptr(stream)))
+        return self.u
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dfmm_graph_destroy(self._h)
             self._h = None
 
     def __del__(self):

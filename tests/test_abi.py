@@ -57,6 +57,9 @@ def test_invalid_arguments_are_rejected_without_a_device(L):
     assert L.dfmm_server_wait(None, 1, 0.0, None) == dfmm.ERR_INVALID
     assert L.dfmm_server_stats(None, None) == dfmm.ERR_INVALID
     assert L.dfmm_server_destroy(None) == dfmm.OK
+    assert L.dfmm_graph_create(None, None, None, 1, None, ctypes.byref(h)) == dfmm.ERR_INVALID
+    assert L.dfmm_graph_launch(None, None) == dfmm.ERR_INVALID
+    assert L.dfmm_graph_destroy(None) == dfmm.OK
     # GMRES: argument checks come before any device call
     it, rr = ctypes.c_int(0), ctypes.c_double(0)
     assert L.dfmm_solve(None, 1.0, 0.0, 1.0, 0.0, None, None, 30, 100, 1e-5, None,

@@ -132,3 +132,19 @@ def test_server_memory_budget_bounds_concurrency(plans):
         tiny.wait(t, timeout=60.0)
     assert e.value.code == -3
     tiny.close()
+
+
+def test_graph_replay_equals_apply(plans):
+    """dfmm_graph_*: the captured apply recomputes u from the current f."""
+    import torch
+    p, _ = plans[2]
+    f = torch.as_tensor(workloads.densities(p.N, 2, 300).astype(np.complex64), device="cuda")
+    u = torch.empty_like(f)
+    g = p.graph(f, u)
+    for seed in (301, 302):
+        f.copy_(torch.as_tensor(workloads.densities(p.N, 2, seed).astype(np.complex64)))
+        g.launch()
+        ref = p.apply(f)
+        torch.cuda.synchronize()
+        assert _rel(u.cpu().numpy(), ref.cpu().numpy()) < 1e-6
+    g.close()

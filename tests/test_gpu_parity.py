@@ -146,6 +146,20 @@ def test_degenerate_inputs():
     assert OD.rel_err(u, OD.direct(p, f)) < 1e-5
 
 
+@pytest.mark.parametrize("case", ["torus", "cube", "ellipsoid"])
+def test_other_surfaces_parity(case):
+    """The other surface families of the batched and served forms, small:
+    torus (R, R/4) with K = 2.5 R, a cube surface, a triaxial ellipsoid."""
+    if case == "torus":
+        p, K = workloads.torus(3.0, 18), 7.5
+    elif case == "cube":
+        p, K = workloads.cube_surface(5.0, 47), 5.0
+    else:
+        p, K = workloads.ellipsoid(4.0, 2.0, 1.0, 15), 8.0
+    e_fmm, e_dir, _ = _parity(p, K, 1e-5, seed=6, ntgt=1500)
+    assert e_fmm <= 1e-5 and e_dir <= 1e-5
+
+
 def test_points_outside_domain_rejected():
     from paper_1311_4257_gb300 import DfmmError
     with pytest.raises(DfmmError) as e:
