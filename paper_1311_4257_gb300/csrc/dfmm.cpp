@@ -47,6 +47,7 @@ struct GemmPlan {
   float2* ops = nullptr;
   std::vector<int4> groups;        // (op, first pair, count, 0)
   int2* pairs = nullptr;
+  std::vector<int32_t> h_dst;      // target row of every pair (host), for tile ordering
   int64_t npairs = 0;
   int fam = 0;                     // profiling family
   __half* img = nullptr;           // tensor-core operator image (tensor form only)
@@ -324,6 +325,8 @@ void finish_gemm(GemmPlan& g, const std::vector<int32_t>& op, const std::vector<
     if (cnt[k + 1] > cnt[k]) g.groups.push_back(make_int4(k, (int)cnt[k], (int)(cnt[k + 1] - cnt[k]), 0));
   g.pairs = ar.alloc<int2>(n);
   DFMM_CUDA(cudaMemcpyAsync(g.pairs, sorted.data(), n * sizeof(int2), cudaMemcpyHostToDevice, s));
+  g.h_dst.resize(n);
+  for (int64_t i = 0; i < n; ++i) g.h_dst[i] = sorted[i].y;
   DFMM_CUDA(cudaStreamSynchronize(s));
 }
 
@@ -1062,15 +1065,38 @@ Workspace* get_workspace(dfmm_plan_s* P, cudaStream_t s, int nrhs) {
   return W;
 }
 
+// Work tiles of a stage: runs of up to cols / nrhs pairs of one operator.
+// Pairs of an operator are sorted by target, so an operator's tiles sweep the
+// whole target array; tiles are ordered by block of target rows first and
+// operator second, so that the tiles in flight together touch one block of
+// targets (and the sources near them) and keep those rows in L2.  Blocks hold
+// about 8 MB of target rows.
+std::vector<int4> make_tiles(const GemmPlan& g, int nrhs, int cols) {
+  const int per = std::max(1, cols / nrhs);
+  std::vector<int4> t;
+  std::vector<int64_t> key;
+  const int64_t row_bytes = (int64_t)g.M * 8 * nrhs;
+  const int64_t block_rows = std::max<int64_t>(1, ((int64_t)8 << 20) / std::max<int64_t>(1, row_bytes));
+  for (const int4& grp : g.groups)
+    for (int p = 0; p < grp.z; p += per) {
+      t.push_back(make_int4(grp.x, grp.y + p, std::min(per, grp.z - p), 0));
+      const int64_t blk = g.h_dst.empty() ? 0 : g.h_dst[grp.y + p] / block_rows;
+      key.push_back(blk * (int64_t)(g.nops + 1) + grp.x);
+    }
+  std::vector<int64_t> order(t.size());
+  for (size_t i = 0; i < order.size(); ++i) order[i] = (int64_t)i;
+  std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return key[a] < key[b]; });
+  std::vector<int4> out(t.size());
+  for (size_t i = 0; i < order.size(); ++i) out[i] = t[order[i]];
+  return out;
+}
+
 std::pair<int4*, int64_t> tiles_for(Workspace* W, const GemmPlan& g, int nrhs, int cols, cudaStream_t s) {
   auto key = std::make_pair((const void*)&g, nrhs * 1024 + cols);
   auto it = W->tiles.find(key);
   if (it != W->tiles.end()) return it->second;
   if (W->external) throw Error(DFMM_ERR_INVALID, "work tiles missing from the carved workspace");
-  int per = std::max(1, cols / nrhs);
-  std::vector<int4> t;
-  for (const int4& grp : g.groups)
-    for (int p = 0; p < grp.z; p += per) t.push_back(make_int4(grp.x, grp.y + p, std::min(per, grp.z - p), 0));
+  std::vector<int4> t = make_tiles(g, nrhs, cols);
   int4* d = W->ar.alloc<int4>(std::max<size_t>(1, t.size()));
   if (!t.empty()) DFMM_CUDA(cudaMemcpyAsync(d, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
   W->tiles[key] = {d, (int64_t)t.size()};
@@ -1313,12 +1339,8 @@ size_t carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaS
   for (const GemmPlan* g : all_gemms(P)) {
     if (g->npairs == 0) continue;
     const int cols = (P->opt.m2l_mode == 2 && gemm_tc_supported(g->M, g->Kd)) ? gemm_tc_columns() : 64;
-    const int per = std::max(1, cols / nrhs);
     tl_cols.push_back(cols);
-    std::vector<int4> t;
-    for (const int4& grp : g->groups)
-      for (int q = 0; q < grp.z; q += per) t.push_back(make_int4(grp.x, grp.y + q, std::min(per, grp.z - q), 0));
-    tl.push_back({g, std::move(t)});
+    tl.push_back({g, make_tiles(*g, nrhs, cols)});
   }
   std::vector<int4*> dst(tl.size());
   for (size_t k = 0; k < tl.size(); ++k) dst[k] = (int4*)take(tl[k].second.size() * sizeof(int4));
