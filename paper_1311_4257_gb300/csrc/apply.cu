@@ -256,6 +256,63 @@ __global__ __launch_bounds__(256) void rows_kernel(RowsArgs a) {
   }
 }
 
+// L2P as a flat stream of rows: warp w evaluates the point rows 4w .. 4w+3
+// (1 KB each at rank 128, loaded together as float4 before any arithmetic, so
+// each warp keeps 4 KB in flight); the state rows they dot with are shared by
+// the points of a leaf and mostly hit in L1.
+constexpr int L2P_ROWS = 4;
+
+template <int Q>
+__global__ __launch_bounds__(256) void l2p_kernel(L2PArgs a) {
+  const int64_t r0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * L2P_ROWS;
+  const int lane = threadIdx.x & 31;
+  if (r0 >= a.nrows) return;
+  const int R2 = a.R / 2;
+  float4 v[L2P_ROWS][Q];
+  int2 m[L2P_ROWS];
+#pragma unroll
+  for (int j = 0; j < L2P_ROWS; ++j) {
+    const int64_t r = r0 + j;
+    const bool ok = r < a.nrows;
+    m[j] = ok ? a.map[r] : make_int2(-1, 0);
+    const float4* row = (const float4*)(a.rows + (ok ? r : r0) * a.R);
+#pragma unroll
+    for (int t = 0; t < Q; ++t) {
+      const int q = lane + 32 * t;
+      v[j][t] = (ok && q < R2) ? __ldcs(row + q) : make_float4(0.f, 0.f, 0.f, 0.f);   // streamed once
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < L2P_ROWS; ++j) {
+    if (m[j].x < 0) continue;   // warp-uniform
+    const float4* st = (const float4*)(a.state + (int64_t)m[j].y * a.nrhs * a.R);
+    for (int k = 0; k < a.nrhs; ++k) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int t = 0; t < Q; ++t) {
+        const int q = lane + 32 * t;
+        if (q < R2) {
+          const float4 sv = __ldg(st + (int64_t)k * R2 + q);
+          acc.x = fmaf(v[j][t].x, sv.x, fmaf(-v[j][t].y, sv.y, acc.x));
+          acc.y = fmaf(v[j][t].x, sv.y, fmaf(v[j][t].y, sv.x, acc.y));
+          acc.x = fmaf(v[j][t].z, sv.z, fmaf(-v[j][t].w, sv.w, acc.x));
+          acc.y = fmaf(v[j][t].z, sv.w, fmaf(v[j][t].w, sv.z, acc.y));
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+      }
+      if (lane == 0) {
+        float2* u = a.us + (int64_t)m[j].x * a.nrhs + k;
+        const float2 o = *u;
+        *u = make_float2(o.x + acc.x, o.y + acc.y);
+      }
+    }
+  }
+}
+
 constexpr int P2P_THREADS = 128;
 constexpr int P2P_CHUNK = 512;    // source points staged at a time
 constexpr int P2P_LEAVES = 64;    // U-list entries staged at a time
@@ -432,6 +489,15 @@ void launch_rows(const RowsArgs& a, cudaStream_t s) {
   if (a.njobs == 0) return;
   if (a.R > 256 || a.R % 2) throw Error(-5, "representation rank must be even and at most 256");
   rows_kernel<<<(unsigned)a.njobs, 256, 0, s>>>(a);
+  DFMM_CUDA(cudaGetLastError());
+}
+
+void launch_l2p(const L2PArgs& a, cudaStream_t s) {
+  if (a.nrows == 0) return;
+  if (a.R > 256 || a.R % 2) throw Error(-5, "representation rank must be even and at most 256");
+  const unsigned grid = (unsigned)((a.nrows + 8 * L2P_ROWS - 1) / (8 * L2P_ROWS));
+  if (a.R <= 128) l2p_kernel<2><<<grid, 256, 0, s>>>(a);
+  else l2p_kernel<4><<<grid, 256, 0, s>>>(a);
   DFMM_CUDA(cudaGetLastError());
 }
 

@@ -83,6 +83,18 @@ struct RowsArgs {
 };
 void launch_rows(const RowsArgs& a, cudaStream_t s);
 
+// L2P, one warp per point: us[p_r][rhs] += sum_q rows[r][q] state[s_r][rhs][q]
+// for every row r, with (p_r, s_r) = map[r] (each point has one row).
+struct L2PArgs {
+  const int2* map;           // (point, state row) per row
+  int64_t nrows;
+  const float2* rows;        // [nrows][R]
+  const float2* state;       // [..][nrhs][R]
+  int R, nrhs;               // R even, <= 256
+  float2* us;                // [N][nrhs]
+};
+void launch_l2p(const L2PArgs& a, cudaStream_t s);
+
 // Near field: us[i] += sum over U-list source leaves of G(p_i, p_j) f_j,
 // skipping p_j == p_i.
 struct P2PArgs {

@@ -95,6 +95,8 @@ struct LFLevel {
   int4* l2p_jobs = nullptr;
   int64_t n_l2p = 0;
   float2* l2p_rows = nullptr;
+  int2* l2p_map = nullptr;         // (point, state row) of every L2P row
+  int64_t n_l2p_rows = 0;
   int64_t npts = 0;      // points in the leaves of this level
   int64_t npts_x = 0;    // source points over the X pairs of this level
 };
@@ -890,6 +892,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
     LFLevel& F = P->lf[l];
     std::vector<double> lp;
     std::vector<int4> jobs;
+    std::vector<int2> rmap;
     int64_t row = 0;
     for (int64_t b = 0; b < LV[l].n; ++b) {
       if (!LV[l].h_leaf[b]) continue;
@@ -897,11 +900,14 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
       jobs.push_back(make_int4(LV[l].h_first[b], LV[l].h_count[b], (int)row, (int)b));
       for (int64_t i = LV[l].h_first[b]; i < LV[l].h_first[b] + LV[l].h_count[b]; ++i) {
         for (int d = 0; d < 3; ++d) lp.push_back(sorted_pts[i][d] - c[d]);
+        rmap.push_back(make_int2((int)i, (int)b));
         ++row;
       }
     }
     F.n_l2p = (int64_t)jobs.size();
     F.l2p_jobs = upload(jobs, ar, s);
+    F.n_l2p_rows = row;
+    F.l2p_map = upload(rmap, ar, s);
     F.l2p_rows = ar.alloc<float2>(std::max<int64_t>(1, row) * F.R);
     if (row > 0) {
       ArenaMark mk(ar);
@@ -915,6 +921,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
   for (int la = P->l_lf0; la < nl; ++la) {
     std::vector<double> lp;
     std::vector<int4> jobs;
+    std::vector<int2> rmap;
     int64_t row = 0;
     for (size_t q = 0; q < nW; ++q) {
       int lb = P->Wl[4 * q], b = P->Wl[4 * q + 1], l2 = P->Wl[4 * q + 2], a = P->Wl[4 * q + 3];
@@ -923,6 +930,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
       jobs.push_back(make_int4(LV[lb].h_first[b], LV[lb].h_count[b], (int)row, a));
       for (int64_t i = LV[lb].h_first[b]; i < LV[lb].h_first[b] + LV[lb].h_count[b]; ++i) {
         for (int d = 0; d < 3; ++d) lp.push_back(sorted_pts[i][d] - c[d]);
+        rmap.push_back(make_int2((int)i, (int)b));
         ++row;
       }
     }
@@ -1234,16 +1242,15 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
     LFLevel& F = P->lf[l];
     if (!F.n_l2p) continue;
     R.launch(F_L2P, 8.0 * F.r * F.npts * nrhs, F.npts * (8.0 * F.R + 16.0 * nrhs) + F.n_l2p * 8.0 * F.R * nrhs, [&] {
-      RowsArgs a;
-      a.jobs = F.l2p_jobs;
-      a.njobs = F.n_l2p;
+      L2PArgs a;
+      a.map = F.l2p_map;
+      a.nrows = F.n_l2p_rows;
       a.rows = F.l2p_rows;
       a.state = W->T[l];
       a.R = F.R;
       a.nrhs = nrhs;
       a.us = W->us;
-      a.atomic = 0;
-      launch_rows(a, s);
+      launch_l2p(a, s);
     });
   }
   for (auto& g : P->m2p) {
