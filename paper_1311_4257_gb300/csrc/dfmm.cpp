@@ -1075,16 +1075,20 @@ Workspace* get_workspace(dfmm_plan_s* P, cudaStream_t s, int nrhs) {
 
 // Work tiles of a stage: runs of up to cols / nrhs pairs of one operator.
 // Pairs of an operator are sorted by target, so an operator's tiles sweep the
-// whole target array; tiles are ordered by block of target rows first and
-// operator second, so that the tiles in flight together touch one block of
-// targets (and the sources near them) and keep those rows in L2.  Blocks hold
-// about 8 MB of target rows.
+// whole target array.  When the stage's operators are small enough to stay in
+// L2 (<= 64 MB), tiles are ordered by block of target rows first and operator
+// second, so that the tiles in flight together touch one block of targets
+// (and the sources near them) and keep those rows in L2; blocks hold about
+// 8 MB of target rows.  Otherwise tiles stay in operator order, so that an
+// operator is read from DRAM once for all its tiles.
 std::vector<int4> make_tiles(const GemmPlan& g, int nrhs, int cols) {
   const int per = std::max(1, cols / nrhs);
   std::vector<int4> t;
   std::vector<int64_t> key;
   const int64_t row_bytes = (int64_t)g.M * 8 * nrhs;
-  const int64_t block_rows = std::max<int64_t>(1, ((int64_t)8 << 20) / std::max<int64_t>(1, row_bytes));
+  const bool blocked = (double)g.nops * g.M * g.Kd * 8.0 <= 64.0 * (1 << 20);
+  const int64_t block_rows = blocked ? std::max<int64_t>(1, ((int64_t)8 << 20) / std::max<int64_t>(1, row_bytes))
+                                     : ((int64_t)1 << 40);
   for (const int4& grp : g.groups)
     for (int p = 0; p < grp.z; p += per) {
       t.push_back(make_int4(grp.x, grp.y + p, std::min(per, grp.z - p), 0));
