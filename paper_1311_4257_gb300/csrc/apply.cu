@@ -313,6 +313,67 @@ __global__ __launch_bounds__(256) void l2p_kernel(L2PArgs a) {
   }
 }
 
+// P2M through rows: one warp per leaf, lane l owns the state entries
+// 2 (l + 32 t), 2 (l + 32 t) + 1 (float4 loads); the leaf's point rows are read
+// 4 at a time (4 KB in flight per warp) and weighted by the points' densities
+// (one broadcast load per point and right-hand side).
+template <int Q>
+__global__ __launch_bounds__(256) void p2m_rows_kernel(P2MRowsArgs a) {
+  const int64_t jw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (jw >= a.njobs) return;
+  const int4 job = a.jobs[jw];
+  const int R2 = a.R / 2;
+  const float4* rows = (const float4*)a.rows;
+  float4* st = (float4*)a.state;
+  for (int k0 = 0; k0 < a.nrhs; k0 += 4) {
+    const int nk = min(4, a.nrhs - k0);
+    float4 acc[4][Q];
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk)
+#pragma unroll
+      for (int t = 0; t < Q; ++t) acc[kk][t] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = 0; i < job.y; i += 4) {
+      float4 r[4][Q];
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int t = 0; t < Q; ++t) {
+          const int q = lane + 32 * t;
+          r[j][t] = (i + j < job.y && q < R2) ? __ldcs(rows + (int64_t)(job.z + i + j) * R2 + q)
+                                              : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        if (i + j >= job.y) break;
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+          if (kk >= nk) break;
+          const float2 f = __ldg(a.fs + (int64_t)(job.x + i + j) * a.nrhs + k0 + kk);
+#pragma unroll
+          for (int t = 0; t < Q; ++t) {
+            float4& c = acc[kk][t];
+            const float4 v = r[j][t];
+            c.x = fmaf(v.x, f.x, fmaf(-v.y, f.y, c.x));
+            c.y = fmaf(v.x, f.y, fmaf(v.y, f.x, c.y));
+            c.z = fmaf(v.z, f.x, fmaf(-v.w, f.y, c.z));
+            c.w = fmaf(v.z, f.y, fmaf(v.w, f.x, c.w));
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int kk = 0; kk < 4; ++kk) {
+      if (kk >= nk) break;
+#pragma unroll
+      for (int t = 0; t < Q; ++t) {
+        const int q = lane + 32 * t;
+        if (q < R2) st[((int64_t)job.w * a.nrhs + k0 + kk) * R2 + q] = acc[kk][t];
+      }
+    }
+  }
+}
+
 constexpr int P2P_THREADS = 128;
 constexpr int P2P_CHUNK = 512;    // source points staged at a time
 constexpr int P2P_LEAVES = 64;    // U-list entries staged at a time
@@ -498,6 +559,15 @@ void launch_l2p(const L2PArgs& a, cudaStream_t s) {
   const unsigned grid = (unsigned)((a.nrows + 8 * L2P_ROWS - 1) / (8 * L2P_ROWS));
   if (a.R <= 128) l2p_kernel<2><<<grid, 256, 0, s>>>(a);
   else l2p_kernel<4><<<grid, 256, 0, s>>>(a);
+  DFMM_CUDA(cudaGetLastError());
+}
+
+void launch_p2m_rows(const P2MRowsArgs& a, cudaStream_t s) {
+  if (a.njobs == 0) return;
+  if (a.R > 256 || a.R % 2) throw Error(-5, "representation rank must be even and at most 256");
+  const unsigned grid = (unsigned)((a.njobs + 7) / 8);
+  if (a.R <= 128) p2m_rows_kernel<2><<<grid, 256, 0, s>>>(a);
+  else p2m_rows_kernel<4><<<grid, 256, 0, s>>>(a);
   DFMM_CUDA(cudaGetLastError());
 }
 

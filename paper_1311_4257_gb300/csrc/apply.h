@@ -95,6 +95,19 @@ struct L2PArgs {
 };
 void launch_l2p(const L2PArgs& a, cudaStream_t s);
 
+// P2M through per-point rows: for every leaf job (first point, count, first
+// row, box) and right-hand side k, state[box][k][q] = sum_i rows[row + i][q]
+// fs[first + i][k].
+struct P2MRowsArgs {
+  const int4* jobs;
+  int64_t njobs;
+  const float2* rows;        // [..][R]
+  const float2* fs;          // [N][nrhs]
+  float2* state;             // [boxes][nrhs][R]
+  int R, nrhs;               // R <= 256
+};
+void launch_p2m_rows(const P2MRowsArgs& a, cudaStream_t s);
+
 // Near field: us[i] += sum over U-list source leaves of G(p_i, p_j) f_j,
 // skipping p_j == p_i.
 struct P2PArgs {

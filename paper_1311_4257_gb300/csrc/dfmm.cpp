@@ -96,6 +96,7 @@ struct LFLevel {
   int64_t n_l2p = 0;
   float2* l2p_rows = nullptr;
   int2* l2p_map = nullptr;         // (point, state row) of every L2P row
+  float2* p2m_rows = nullptr;      // outgoing-state rows of the leaf points (same row order as L2P)
   int64_t n_l2p_rows = 0;
   int64_t npts = 0;      // points in the leaves of this level
   int64_t npts_x = 0;    // source points over the X pairs of this level
@@ -552,27 +553,16 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
     const int R = F.R;
     F.chk_a2 = upload_chk(rp.a2, 2 * rp.r, ar, s);
     F.chk_b2 = upload_chk(rp.b2, 2 * rp.r, ar, s);
-    F.p2m.M = R; F.p2m.Kd = 2 * R; F.p2m.nops = 1;
-    F.p2m.ops = upload_projection(rp.Qo, rp.r, rp.wa2.data(), R, ar, s);
     F.p2l.M = R; F.p2l.Kd = 2 * R; F.p2l.nops = 1;
     F.p2l.ops = upload_projection(rp.Qi, rp.r, nullptr, R, ar, s);
     std::vector<int4> jobs;
     std::vector<int32_t> op;
     std::vector<int2> pr;
-    // P2M: leaves of this level
+    // P2M: leaves of this level, through per-point rows (formed with the L2P
+    // rows below)
     for (int64_t b = 0; b < LV[l].n; ++b)
-      if (LV[l].h_leaf[b]) {
-        jobs.push_back(make_int4(LV[l].h_first[b], LV[l].h_count[b], (int)jobs.size(), 0));
-        op.push_back(0);
-        pr.push_back(make_int2((int)jobs.size() - 1, (int)b));
-      }
-    F.n_p2m = (int64_t)jobs.size();
-    for (auto& j : jobs) F.npts += j.y;
-    F.p2m_jobs = upload(jobs, ar, s);
-    F.p2m.fam = F_P2M_PROJ;
-    F.p2m.flops_rhs = 8.0 * rp.r * 2 * rp.r * F.n_p2m;
-    finish_gemm(F.p2m, op, pr, ar, s);
-    other_flops += 8.0 * rp.r * 2 * rp.r * F.n_p2m;
+      if (LV[l].h_leaf[b]) F.npts += LV[l].h_count[b];
+    other_flops += 8.0 * rp.r * F.npts;
     // P2L: X pairs whose target is at this level
     {
       std::vector<int4> xj;
@@ -909,11 +899,13 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
     F.n_l2p_rows = row;
     F.l2p_map = upload(rmap, ar, s);
     F.l2p_rows = ar.alloc<float2>(std::max<int64_t>(1, row) * F.R);
+    F.p2m_rows = ar.alloc<float2>(std::max<int64_t>(1, row) * F.R);
     if (row > 0) {
       ArenaMark mk(ar);
       double* dlp = ar.alloc<double>(lp.size());
       DFMM_CUDA(cudaMemcpyAsync(dlp, lp.data(), lp.size() * 8, cudaMemcpyHostToDevice, s));
       form_rows(true, dreps[ridx.at({l, -1})], dlp, row, F.l2p_rows, cb, ar, s);
+      form_p2m_rows(dreps[ridx.at({l, -1})], dlp, row, F.p2m_rows, cb, ar, s);
     }
     other_flops += 8.0 * F.r * (double)row;
   }
@@ -1177,23 +1169,19 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
   // 1. LF upward: P2M at leaves, LF-M2M from the level below
   for (int l = nl - 1; l >= P->l_lf0; --l) {
     LFLevel& F = P->lf[l];
-    if (F.n_p2m) {
-      double ev = (double)F.npts * 2 * F.r;
-      R.launch(F_P2M_EVAL, ev * (16 + 8.0 * nrhs), F.npts * (16.0 + 8.0 * nrhs) + F.n_p2m * 2.0 * F.R * 8 * nrhs, [&] {
-        P2CArgs a;
-        a.jobs = F.p2m_jobs;
-        a.njobs = F.n_p2m;
-        a.shifts = P->zero_shift;
-        a.chk = F.chk_a2;
-        a.nchk = 2 * F.r;
-        a.ld = 2 * F.R;
-        a.pts = P->pts_local;
-        a.fs = W->fs;
-        a.out = W->p2m;
-        a.nrhs = nrhs;
-        launch_p2c(a, s);
-      });
-      R.gemm(F.p2m, count ? nullptr : W->p2m, 2 * F.R, F.n_p2m, S(l), F.R);
+    if (F.n_l2p) {   // P2M: every leaf of this level, through its points' rows
+      R.launch(F_P2M_EVAL, 8.0 * F.r * F.npts * nrhs, F.npts * (8.0 * F.R + 8.0 * nrhs) + F.n_l2p * 8.0 * F.R * nrhs,
+               [&] {
+                 P2MRowsArgs a;
+                 a.jobs = F.l2p_jobs;
+                 a.njobs = F.n_l2p;
+                 a.rows = F.p2m_rows;
+                 a.fs = W->fs;
+                 a.state = W->S[l];
+                 a.R = F.R;
+                 a.nrhs = nrhs;
+                 launch_p2m_rows(a, s);
+               });
     }
     if (l + 1 < nl) R.gemm(F.m2m, S(l + 1), P->lf[l + 1].R, P->lf[l + 1].nbox, S(l), F.R);
   }

@@ -216,4 +216,29 @@ void form_rows(bool incoming, const DevRep& rep, const double* d_pts, int64_t n,
   DFMM_CUDA(cudaStreamSynchronize(s));
 }
 
+void form_p2m_rows(const DevRep& rep, const double* d_pts, int64_t n, float2* out, cublasHandle_t cb, DevArena& ar,
+                   cudaStream_t s) {
+  if (n <= 0) return;
+  ArenaMark mark(ar);
+  const int R = rep.R, K2 = 2 * R;
+  int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)((512ull << 20) / (3 * R * sizeof(double2)))));
+  double2* K = ar.alloc<double2>((size_t)chunk * K2);
+  double2* T = ar.alloc<double2>((size_t)chunk * R);
+  const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
+  DFMM_CUBLAS(cublasSetStream(cb, s));
+  for (int64_t st = 0; st < n; st += chunk) {
+    const int64_t m = std::min(chunk, n - st);
+    const int64_t ne = m * K2;
+    // K (m x 2R, row-major): G(y_i - c, a2_p) for the 2r check points, zero padded
+    rows_kmat_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(d_pts + 3 * st, m, rep.a2, nullptr, 2 * rep.r, K2,
+                                                                   K);
+    // row-major T (m x R) = K (m x 2R) PoutH^T, PoutH = Qo^H W (R x 2R, row-major)
+    DFMM_CUBLAS(cublasZgemm(cb, CUBLAS_OP_T, CUBLAS_OP_N, R, (int)m, K2, &one, (const cuDoubleComplex*)rep.PoutH,
+                            K2, (const cuDoubleComplex*)K, K2, &zero, (cuDoubleComplex*)T, R));
+    to_c64_kernel<<<(unsigned)((m * R + 255) / 256), 256, 0, s>>>(T, out + st * R, m * R);
+    DFMM_CUDA(cudaGetLastError());
+  }
+  DFMM_CUDA(cudaStreamSynchronize(s));
+}
+
 }  // namespace dfmm

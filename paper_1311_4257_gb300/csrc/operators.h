@@ -48,4 +48,11 @@ void form_ops(OpKind kind, const std::vector<OpSpec>& ops, const std::vector<Dev
 void form_rows(bool incoming, const DevRep& rep, const double* d_local_pts, int64_t n, float2* out,
                cublasHandle_t cb, DevArena& ar, cudaStream_t s);
 
+// Rows of P2M through the outgoing representation (Eq. 2 with the
+// least-squares projection): row_i = Qo^H W G(a2, y_i - c), the outgoing
+// state a unit source at y_i produces.  pts: device FP64 [n][3] of y_i - c;
+// written as complex64 [n][R].
+void form_p2m_rows(const DevRep& rep, const double* d_local_pts, int64_t n, float2* out, cublasHandle_t cb,
+                   DevArena& ar, cudaStream_t s);
+
 }  // namespace dfmm
