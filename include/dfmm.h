@@ -284,8 +284,8 @@ int dfmm_server_destroy(dfmm_server_t server);
  *   enable == 0 : stop, synchronise `stream`, and write the totals since
  *                 recording started into out[0 .. *n) (cap entries at most),
  *                 one entry per kernel family:
- *                 m2l_hf, m2l_lf, m2m, l2l, p2m_proj, p2l_proj, p2m_eval,
- *                 p2l_eval, l2p, m2p, p2p, permute, zero.
+ *                 m2l_hf, m2l_lf, m2m, l2l, p2l_proj, p2m_eval, p2l_eval,
+ *                 l2p, m2p, p2p, permute, zero, split.
  *   flops and bytes are algorithmic: 8 r_t r_s per (pair, right-hand side)
  *   for the translations with the unpadded ranks; every operator, source
  *   state and target state counted once per launch; for P2P 16 + 8 nrhs

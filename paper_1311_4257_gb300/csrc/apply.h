@@ -27,6 +27,8 @@ struct GemmArgs {
   float2* dst;              // rows of dst_ld complex
   int src_ld, dst_ld;
   int nrhs;
+  int store;                // 1: every target row of the stage has one pair and nothing wrote it
+                            //    earlier in the apply, so results are stored, not added
 };
 
 void launch_gemm_stage(const GemmArgs& a, cudaStream_t s);

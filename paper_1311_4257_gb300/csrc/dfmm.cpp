@@ -48,6 +48,7 @@ struct GemmPlan {
   std::vector<int4> groups;        // (op, first pair, count, 0)
   int2* pairs = nullptr;
   std::vector<int32_t> h_dst;      // target row of every pair (host), for tile ordering
+  bool dst_unique = false;         // no two pairs share a target row
   int64_t npairs = 0;
   int fam = 0;                     // profiling family
   __half* img = nullptr;           // tensor-core operator image (tensor form only)
@@ -57,9 +58,9 @@ struct GemmPlan {
   double bytes_rhs = 0;            // unique source rows + target rows (read and write), per rhs
 };
 
-enum Fam { F_M2L_HF, F_M2L_LF, F_M2M, F_L2L, F_P2M_PROJ, F_P2L_PROJ, F_P2M_EVAL, F_P2L_EVAL, F_L2P, F_M2P, F_P2P,
+enum Fam { F_M2L_HF, F_M2L_LF, F_M2M, F_L2L, F_P2L_PROJ, F_P2M_EVAL, F_P2L_EVAL, F_L2P, F_M2P, F_P2P,
            F_PERMUTE, F_ZERO, F_SPLIT, F_COUNT };
-const char* kFamName[F_COUNT] = {"m2l_hf", "m2l_lf", "m2m", "l2l", "p2m_proj", "p2l_proj", "p2m_eval",
+const char* kFamName[F_COUNT] = {"m2l_hf", "m2l_lf", "m2m", "l2l", "p2l_proj", "p2m_eval",
                                  "p2l_eval", "l2p", "m2p", "p2p", "permute", "zero", "split"};
 
 struct ProfRec {
@@ -84,11 +85,8 @@ struct LFLevel {
   double w = 0;
   int R = 0, r = 0;
   int64_t nbox = 0;
-  GemmPlan m2m, l2l, v, p2m, p2l;   // m2m from l+1, l2l from l-1 (LF or HF)
-  ChkPt* chk_a2 = nullptr;
+  GemmPlan m2m, l2l, v, p2l;   // m2m from l+1, l2l from l-1 (LF or HF)
   ChkPt* chk_b2 = nullptr;
-  int4* p2m_jobs = nullptr;
-  int64_t n_p2m = 0;
   int4* p2l_jobs = nullptr;
   float4* p2l_shifts = nullptr;
   int64_t n_p2l = 0;
@@ -115,7 +113,7 @@ struct Workspace {
   int nrhs = 0;
   bool external = false;   // buffers carved from caller-provided memory
   DevArena ar;
-  float2 *fs = nullptr, *us = nullptr, *p2m = nullptr, *p2l = nullptr;
+  float2 *fs = nullptr, *us = nullptr, *p2l = nullptr;
   __half *ahi = nullptr, *alo = nullptr;                // split source buffer (tensor form)
   float* ascale = nullptr;                              // its per-row scales
   std::vector<float2*> S, T;                            // per level (LF or HF states)
@@ -317,6 +315,7 @@ void finish_gemm(GemmPlan& g, const std::vector<int32_t>& op, const std::vector<
     for (auto u : used) uops += u;
     g.bytes_fixed = (double)uops * g.M * g.Kd * 8.0;
     g.bytes_rhs = (double)ua * g.Kd * 8.0 + 2.0 * (double)ub * g.M * 8.0;
+    g.dst_unique = ub == n;
   }
   std::vector<int64_t> cnt(g.nops + 1, 0);
   for (int64_t i = 0; i < n; ++i) cnt[op[i] + 1]++;
@@ -551,7 +550,6 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
     F.nbox = LV[l].n;
     const Rep& rp = P->reps->get(F.w, -1);
     const int R = F.R;
-    F.chk_a2 = upload_chk(rp.a2, 2 * rp.r, ar, s);
     F.chk_b2 = upload_chk(rp.b2, 2 * rp.r, ar, s);
     F.p2l.M = R; F.p2l.Kd = 2 * R; F.p2l.nops = 1;
     F.p2l.ops = upload_projection(rp.Qi, rp.r, nullptr, R, ar, s);
@@ -992,7 +990,7 @@ int64_t max_source_rows(const dfmm_plan_s* P) {
   int64_t m = 1;
   for (int l = 0; l < P->nl; ++l) {
     if (l >= P->l_lf0) {
-      m = std::max({m, P->lf[l].nbox, P->lf[l].n_p2m, P->lf[l].n_p2l});
+      m = std::max({m, P->lf[l].nbox, P->lf[l].n_p2l});
     } else if (P->l_top >= 0 && l >= P->l_top) {
       m = std::max(m, (int64_t)std::max(P->hf[l].out_keys.size(), P->hf[l].in_keys.size()));
     }
@@ -1008,7 +1006,6 @@ int64_t max_source_elems(const dfmm_plan_s* P) {
     if (l >= P->l_lf0) {
       const LFLevel& F = P->lf[l];
       m = std::max(m, F.nbox * (int64_t)F.R);
-      m = std::max(m, F.n_p2m * 2 * (int64_t)F.R);
       m = std::max(m, F.n_p2l * 2 * (int64_t)F.R);
     } else if (P->l_top >= 0 && l >= P->l_top) {
       const HFLevel& H = P->hf[l];
@@ -1032,7 +1029,7 @@ Workspace* get_workspace(dfmm_plan_s* P, cudaStream_t s, int nrhs) {
   W->zero.push_back({W->us, (size_t)N * nrhs * sizeof(float2)});
   W->S.assign(P->nl, nullptr);
   W->T.assign(P->nl, nullptr);
-  int64_t p2m_rows = 1, p2l_rows = 1;
+  int64_t p2l_rows = 1;
   for (int l = 0; l < P->nl; ++l) {
     int64_t rows = 0;
     int R = 0;
@@ -1048,10 +1045,8 @@ Workspace* get_workspace(dfmm_plan_s* P, cudaStream_t s, int nrhs) {
     W->T[l] = ar.alloc<float2>(rows * nrhs * R);
     W->zero.push_back({W->S[l], (size_t)rows * nrhs * R * 8});
     W->zero.push_back({W->T[l], (size_t)rows * nrhs * R * 8});
-    p2m_rows = std::max(p2m_rows, P->lf[l].n_p2m * 2 * R);
     p2l_rows = std::max(p2l_rows, P->lf[l].n_p2l * 2 * R);
   }
-  W->p2m = ar.alloc<float2>(p2m_rows * nrhs);
   W->p2l = ar.alloc<float2>(p2l_rows * nrhs);
   if (P->opt.m2l_mode == 2) {
     int64_t e = max_source_elems(P) * nrhs * 2;
@@ -1121,7 +1116,10 @@ struct Runner {
     fn();
   }
 
-  void gemm(const GemmPlan& g, const float2* src, int src_ld, int64_t src_rows, float2* dst, int dst_ld) {
+  // first: no earlier stage of the apply writes dst (it holds zeros), so a stage whose
+  // target rows are all distinct may store its results instead of adding them
+  void gemm(const GemmPlan& g, const float2* src, int src_ld, int64_t src_rows, float2* dst, int dst_ld,
+            bool first = false) {
     if (g.npairs == 0) return;
     if (count) { count[0] += (P->opt.m2l_mode == 2 && gemm_tc_supported(g.M, g.Kd)) ? 2 : 1; return; }
     const bool tc = P->opt.m2l_mode == 2 && gemm_tc_supported(g.M, g.Kd);
@@ -1138,6 +1136,7 @@ struct Runner {
     a.src_ld = src_ld;
     a.dst_ld = dst_ld;
     a.nrhs = nrhs;
+    a.store = (first && g.dst_unique) ? 1 : 0;
     if (tc) {
       {
         ProfScope ps(W, s, F_SPLIT, 0.0, (double)src_rows * nrhs * src_ld * 16);
@@ -1196,7 +1195,8 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
     // 3. HF downward: L2L from the parent level, then M2L
     for (int l = P->l_top; l <= P->l1; ++l) {
       HFLevel& H = P->hf[l];
-      if (l > P->l_top) R.gemm(H.l2l, T(l - 1), P->hf[l - 1].R, (int64_t)P->hf[l - 1].in_keys.size(), T(l), H.R);
+      if (l > P->l_top)
+        R.gemm(H.l2l, T(l - 1), P->hf[l - 1].R, (int64_t)P->hf[l - 1].in_keys.size(), T(l), H.R, true);
       R.gemm(H.m2l, S(l), H.R, (int64_t)H.out_keys.size(), T(l), H.R);
     }
   }
@@ -1205,9 +1205,9 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
     LFLevel& F = P->lf[l];
     if (l == P->l_lf0) {
       if (P->l_top >= 0)
-        R.gemm(F.l2l, T(P->l1), P->hf[P->l1].R, (int64_t)P->hf[P->l1].in_keys.size(), T(l), F.R);
+        R.gemm(F.l2l, T(P->l1), P->hf[P->l1].R, (int64_t)P->hf[P->l1].in_keys.size(), T(l), F.R, true);
     } else {
-      R.gemm(F.l2l, T(l - 1), P->lf[l - 1].R, P->lf[l - 1].nbox, T(l), F.R);
+      R.gemm(F.l2l, T(l - 1), P->lf[l - 1].R, P->lf[l - 1].nbox, T(l), F.R, true);
     }
     R.gemm(F.v, S(l), F.R, F.nbox, T(l), F.R);
     if (F.n_p2l) {
@@ -1280,7 +1280,7 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
 // Every translation stage of the plan, for laying out work tiles.
 std::vector<const GemmPlan*> all_gemms(dfmm_plan_s* P) {
   std::vector<const GemmPlan*> v;
-  for (auto& F : P->lf) { v.push_back(&F.m2m); v.push_back(&F.l2l); v.push_back(&F.v); v.push_back(&F.p2m); v.push_back(&F.p2l); }
+  for (auto& F : P->lf) { v.push_back(&F.m2m); v.push_back(&F.l2l); v.push_back(&F.v); v.push_back(&F.p2l); }
   for (auto& H : P->hf) { v.push_back(&H.m2m); v.push_back(&H.m2l); v.push_back(&H.l2l); }
   return v;
 }
@@ -1306,7 +1306,7 @@ size_t carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaS
   W.zero.push_back({W.us, (size_t)N * nrhs * 8});
   W.S.assign(P->nl, nullptr);
   W.T.assign(P->nl, nullptr);
-  size_t p2m_rows = 1, p2l_rows = 1;
+  size_t p2l_rows = 1;
   for (int l = 0; l < P->nl; ++l) {
     if (l >= P->l_lf0) {
       size_t b = (size_t)P->lf[l].nbox * nrhs * P->lf[l].R * 8;
@@ -1314,7 +1314,6 @@ size_t carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaS
       W.T[l] = (float2*)take(b);
       W.zero.push_back({W.S[l], b});
       W.zero.push_back({W.T[l], b});
-      p2m_rows = std::max(p2m_rows, (size_t)P->lf[l].n_p2m * 2 * P->lf[l].R);
       p2l_rows = std::max(p2l_rows, (size_t)P->lf[l].n_p2l * 2 * P->lf[l].R);
     } else if (P->l_top >= 0 && l >= P->l_top) {
       size_t so = P->hf[l].out_keys.size(), si = P->hf[l].in_keys.size();
@@ -1323,7 +1322,6 @@ size_t carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaS
       if (si) { W.T[l] = (float2*)take(si * nrhs * R * 8); W.zero.push_back({W.T[l], si * nrhs * R * 8}); }
     }
   }
-  W.p2m = (float2*)take(p2m_rows * nrhs * 8);
   W.p2l = (float2*)take(p2l_rows * nrhs * 8);
   if (P->opt.m2l_mode == 2) {
     size_t e = (size_t)max_source_elems(P) * nrhs * 2;

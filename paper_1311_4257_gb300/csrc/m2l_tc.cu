@@ -450,9 +450,14 @@ __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcAr
         tmem_ld16_pair(trow + (uint32_t)j0, trow + 256u + (uint32_t)j0, v, w);
         if (out) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            red_add4(out + j0 + 4 * q, (v[4 * q] + w[4 * q]) * cs, (v[4 * q + 1] + w[4 * q + 1]) * cs,
-                     (v[4 * q + 2] + w[4 * q + 2]) * cs, (v[4 * q + 3] + w[4 * q + 3]) * cs);
+          for (int q = 0; q < 4; ++q) {
+            const float4 r = make_float4((v[4 * q] + w[4 * q]) * cs, (v[4 * q + 1] + w[4 * q + 1]) * cs,
+                                         (v[4 * q + 2] + w[4 * q + 2]) * cs, (v[4 * q + 3] + w[4 * q + 3]) * cs);
+            if (a.store)
+              *(float4*)(out + j0 + 4 * q) = r;
+            else
+              red_add4(out + j0 + 4 * q, r.x, r.y, r.z, r.w);
+          }
         }
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
