@@ -1116,13 +1116,19 @@ struct Runner {
     fn();
   }
 
+  int split_key = -1;   // source buffer that the split arrays hold (tensor form), -1: none
+
+  // src_key names the source buffer (kSrcS / kSrcT + level, -1 for one used once); a
+  // stage whose source is the buffer split for the previous stage reuses that split.
   // first: no earlier stage of the apply writes dst (it holds zeros), so a stage whose
-  // target rows are all distinct may store its results instead of adding them
+  // target rows are all distinct may store its results instead of adding them.
   void gemm(const GemmPlan& g, const float2* src, int src_ld, int64_t src_rows, float2* dst, int dst_ld,
-            bool first = false) {
+            int src_key, bool first = false) {
     if (g.npairs == 0) return;
-    if (count) { count[0] += (P->opt.m2l_mode == 2 && gemm_tc_supported(g.M, g.Kd)) ? 2 : 1; return; }
     const bool tc = P->opt.m2l_mode == 2 && gemm_tc_supported(g.M, g.Kd);
+    const bool split = tc && (src_key < 0 || src_key != split_key);
+    if (tc) split_key = src_key;
+    if (count) { count[0] += split ? 2 : 1; return; }
     auto t = tiles_for(W, g, nrhs, tc ? gemm_tc_columns() : 64, s);
     GemmArgs a;
     a.ops = g.ops;
@@ -1138,7 +1144,7 @@ struct Runner {
     a.nrhs = nrhs;
     a.store = (first && g.dst_unique) ? 1 : 0;
     if (tc) {
-      {
+      if (split) {
         ProfScope ps(W, s, F_SPLIT, 0.0, (double)src_rows * nrhs * src_ld * 16);
         launch_split(src, src_rows * nrhs, src_ld, W->ahi, W->alo, W->ascale, s);
       }
@@ -1151,6 +1157,8 @@ struct Runner {
     }
   }
 };
+
+constexpr int kSrcS = 0, kSrcT = 64;   // source keys: outgoing / incoming states of a level
 
 void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_t s, int64_t* count = nullptr,
                Workspace* ext = nullptr) {
@@ -1182,22 +1190,27 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
                  launch_p2m_rows(a, s);
                });
     }
-    if (l + 1 < nl) R.gemm(F.m2m, S(l + 1), P->lf[l + 1].R, P->lf[l + 1].nbox, S(l), F.R);
+    if (l + 1 < nl) R.gemm(F.m2m, S(l + 1), P->lf[l + 1].R, P->lf[l + 1].nbox, S(l), F.R, kSrcS + l + 1);
   }
-  // 2. HF upward
+  // M2L of each level as soon as its outgoing states are complete, so that the
+  // next M2M, which reads the same states, reuses their split.  The V list of the
+  // top LF level: its L2L (from HF, summed over directions) adds anyway.
+  if (P->l_lf0 < nl)
+    R.gemm(P->lf[P->l_lf0].v, S(P->l_lf0), P->lf[P->l_lf0].R, P->lf[P->l_lf0].nbox, T(P->l_lf0),
+           P->lf[P->l_lf0].R, kSrcS + P->l_lf0);
+  // 2. HF upward: M2M, then that level's M2L
   if (P->l_top >= 0) {
     for (int l = P->l1; l >= P->l_top; --l) {
       HFLevel& H = P->hf[l];
       int sld = (l == P->l1) ? P->lf[l + 1].R : P->hf[l + 1].R;
       int64_t srows = (l == P->l1) ? P->lf[l + 1].nbox : (int64_t)P->hf[l + 1].out_keys.size();
-      R.gemm(H.m2m, S(l + 1), sld, srows, S(l), H.R);
+      R.gemm(H.m2m, S(l + 1), sld, srows, S(l), H.R, kSrcS + l + 1);
+      R.gemm(H.m2l, S(l), H.R, (int64_t)H.out_keys.size(), T(l), H.R, kSrcS + l);
     }
-    // 3. HF downward: L2L from the parent level, then M2L
-    for (int l = P->l_top; l <= P->l1; ++l) {
+    // 3. HF downward: L2L from the parent level
+    for (int l = P->l_top + 1; l <= P->l1; ++l) {
       HFLevel& H = P->hf[l];
-      if (l > P->l_top)
-        R.gemm(H.l2l, T(l - 1), P->hf[l - 1].R, (int64_t)P->hf[l - 1].in_keys.size(), T(l), H.R, true);
-      R.gemm(H.m2l, S(l), H.R, (int64_t)H.out_keys.size(), T(l), H.R);
+      R.gemm(H.l2l, T(l - 1), P->hf[l - 1].R, (int64_t)P->hf[l - 1].in_keys.size(), T(l), H.R, kSrcT + l - 1);
     }
   }
   // 4. LF downward
@@ -1205,11 +1218,11 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
     LFLevel& F = P->lf[l];
     if (l == P->l_lf0) {
       if (P->l_top >= 0)
-        R.gemm(F.l2l, T(P->l1), P->hf[P->l1].R, (int64_t)P->hf[P->l1].in_keys.size(), T(l), F.R, true);
+        R.gemm(F.l2l, T(P->l1), P->hf[P->l1].R, (int64_t)P->hf[P->l1].in_keys.size(), T(l), F.R, kSrcT + P->l1);
     } else {
-      R.gemm(F.l2l, T(l - 1), P->lf[l - 1].R, P->lf[l - 1].nbox, T(l), F.R, true);
+      R.gemm(F.l2l, T(l - 1), P->lf[l - 1].R, P->lf[l - 1].nbox, T(l), F.R, kSrcT + l - 1, true);
+      R.gemm(F.v, S(l), F.R, F.nbox, T(l), F.R, kSrcS + l);
     }
-    R.gemm(F.v, S(l), F.R, F.nbox, T(l), F.R);
     if (F.n_p2l) {
       double ev = (double)F.npts_x * 2 * F.r;
       R.launch(F_P2L_EVAL, ev * (16 + 8.0 * nrhs), F.npts_x * (16.0 + 8.0 * nrhs) + F.n_p2l * 2.0 * F.R * 8 * nrhs, [&] {
@@ -1226,7 +1239,7 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
         a.nrhs = nrhs;
         launch_p2c(a, s);
       });
-      R.gemm(F.p2l, count ? nullptr : W->p2l, 2 * F.R, F.n_p2l, T(l), F.R);
+      R.gemm(F.p2l, count ? nullptr : W->p2l, 2 * F.R, F.n_p2l, T(l), F.R, -1);
     }
   }
   // 5. L2P at every leaf, M2P over the W list
