@@ -29,7 +29,9 @@
 //    many bytes as the complex64 operator), and the source states are split
 //    by a pass before the stage.  Each stage's operator tile arrives by one
 //    bulk copy (cp.async.bulk, completing on an mbarrier), the gathered state
-//    rows by 16-byte asynchronous copies (cp.async); 4 stages of 32 K-values.
+//    rows by 16-byte asynchronous copies (cp.async), 8 lanes per row so that
+//    one warp-wide copy reads 4 rows x 2 contiguous 64-byte segments instead of
+//    32 scattered pieces; 4 stages of 32 K-values.
 //  * One thread issues the MMAs and commits them to an mbarrier; stage reuse
 //    waits on it with a time limit.  The epilogue reads the accumulators with
 //    tcgen05.ld (row = gathered column) and scatter-adds them into the target
@@ -47,7 +49,7 @@ namespace {
 constexpr int TC_M = 128;
 constexpr int TC_BK = 32;                          // K values (fp16) per stage
 constexpr int TC_NMAX = 256;
-constexpr int TC_PRODUCERS = 128;                 // warps 0-3: one gathered row each
+constexpr int TC_PRODUCERS = 128;                 // warps 0-3: gather the 128 rows of a chunk
 constexpr int TC_MMA_WARP = 8;                     // warps 4-7: epilogue; warp 8: MMA issuer
 constexpr int TC_THREADS = 288;
 constexpr int TC_STAGES = 4;
@@ -277,8 +279,9 @@ __device__ __forceinline__ bool mbar_wait_drain(uint32_t bar, uint32_t parity) {
 
 // Persistent, warp-specialised stage kernel.  Work item = (tile, N block);
 // CTA x takes items x, x + gridDim.x, ...  Roles:
-//   warps 0-3  producers: thread r gathers gathered row r of each K chunk
-//              (cp.async, completion counted on the stage's full barrier),
+//   warps 0-3  producers: 8 threads gather one row's K chunk (its 64-byte hi
+//              and lo segments, 16 bytes each), 8 rows per thread (cp.async,
+//              completion counted on the stage's full barrier),
 //              thread 0 also bulk-copies the operator tile; they run up to
 //              TC_STAGES chunks ahead, across items.
 //   warp 8     one thread issues the MMAs of a chunk once its stage is full,
@@ -338,10 +341,19 @@ __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcAr
       const int b = (int)(it % nb);
       const int n = min(TC_NMAX, 2 * a.M - TC_NMAX * b);
       const __half* img = t.img + tile.x * op_elems + (int64_t)b * nchunk * 2 * TC_NMAX * TC_BK;
-      int64_t sr = -1;
-      if (tid < tile.z * a.nrhs) sr = (int64_t)a.pairs[tile.y + tid / a.nrhs].x * a.nrhs + tid % a.nrhs;
-      const __half* rh = t.src_hi + (sr < 0 ? 0 : sr) * Kreal;
-      const __half* rl = t.src_lo + (sr < 0 ? 0 : sr) * Kreal;
+      // thread tid copies 16-byte piece (tid & 3) of the hi (tid & 4 == 0) or lo
+      // half-line of rows (tid >> 3) + 16 q: 8 lanes cover one row's chunk, so a
+      // warp's copy touches 4 rows x 2 segments of 64 bytes
+      const int piece = tid & 3, which = (tid >> 2) & 1;
+      const __half* srow[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int row = (tid >> 3) + 16 * q;
+        srow[q] = nullptr;
+        if (row < tile.z * a.nrhs)
+          srow[q] = (which ? t.src_lo : t.src_hi) +
+                    ((int64_t)a.pairs[tile.y + row / a.nrhs].x * a.nrhs + row % a.nrhs) * Kreal + 8 * piece;
+      }
       for (int c = 0; c < nchunk; ++c, ++g) {
         const int st = (int)(g % TC_STAGES);
         const int64_t j = g / TC_STAGES;
@@ -353,17 +365,14 @@ __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcAr
         }
         const uint32_t sA = sbase + st * STAGE_BYTES;
         const int k0 = c * TC_BK;
+        const bool kin = k0 + 8 * piece < Kreal;
 #pragma unroll
-        for (int piece = 0; piece < 4; ++piece) {
-          const int k = k0 + 8 * piece;
-          const uint32_t dh = sA + kmaj_off(tid, 8 * piece);
-          if (sr >= 0 && k < Kreal) {
-            cp_async16(dh, rh + k);
-            cp_async16(dh + A_BYTES, rl + k);
-          } else {
+        for (int q = 0; q < 8; ++q) {
+          const uint32_t dh = sA + (uint32_t)which * A_BYTES + kmaj_off((tid >> 3) + 16 * q, 8 * piece);
+          if (srow[q] && kin)
+            cp_async16(dh, srow[q] + k0);
+          else
             cp_async16_zero(dh, t.src_hi);
-            cp_async16_zero(dh + A_BYTES, t.src_lo);
-          }
         }
         asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[st])) : "memory");
         if (tid == 0) {   // operator tile: hi then lo, n x 32 values each
