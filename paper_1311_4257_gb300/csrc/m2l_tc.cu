@@ -34,8 +34,10 @@
 //    32 scattered pieces; 4 stages of 32 K-values.
 //  * One thread issues the MMAs and commits them to an mbarrier; stage reuse
 //    waits on it with a time limit.  The epilogue reads the accumulators with
-//    tcgen05.ld (row = gathered column) and scatter-adds them into the target
-//    states with return-free vector reductions.
+//    tcgen05.ld in the .16x256b shape (TMEM lane = gathered column; four lanes
+//    of a warp hold 8 consecutive outputs of one column) and scatter-adds them
+//    into the target states with return-free 8-byte reductions, so one warp
+//    instruction covers 8 target rows x 32 contiguous bytes.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -133,12 +135,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
                : "memory");
 }
 
-// fire-and-forget vector add to global memory (no value returned)
-__device__ __forceinline__ void red_add4(float* p, float a, float b, float c, float d) {
-  asm volatile("red.relaxed.gpu.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
-               : "memory");
-}
-
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
@@ -146,25 +142,20 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b,
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
-// two 16-column loads (one per accumulator), one wait
-__device__ __forceinline__ void tmem_ld16_pair(uint32_t ta, uint32_t tb, float* v, float* w) {
-  uint32_t r[16], q[16];
+// 16 lanes x 32 columns of one accumulator (.16x256b, 4 repetitions): thread t
+// gets lane t/4 (r[4j], r[4j+1]) and lane t/4 + 8 (r[4j+2], r[4j+3]) at columns
+// 8j + 2 (t % 4) + {0, 1}
+__device__ __forceinline__ void tmem_ld16x256_x4(uint32_t ta, uint32_t* r) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      "tcgen05.ld.sync.aligned.16x256b.x4.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(ta));
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]),
-        "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15])
-      : "r"(tb));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 16; ++i) {
-    v[i] = __uint_as_float(r[i]);
-    w[i] = __uint_as_float(q[i]);
-  }
+}
+
+// fire-and-forget add of two floats to global memory (no value returned)
+__device__ __forceinline__ void red_add2(float* p, float a, float b) {
+  asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
 }
 
 // smallest power of two >= m (1 for m == 0)
@@ -289,8 +280,9 @@ __device__ __forceinline__ bool mbar_wait_drain(uint32_t bar, uint32_t parity) {
 //              item's last chunk to acc_full; it waits for acc_empty before
 //              it overwrites the accumulators with the next item.
 //   warps 4-7  epilogue: read the accumulators (warp 4 + q reads TMEM lanes
-//              32q..32q+31 = gathered columns), release them (acc_empty) and
-//              scatter-add into the target states.
+//              32q..32q+31 = gathered columns, as two 16-lane blocks of the
+//              .16x256b shape), scatter-add into the target states and then
+//              release them (acc_empty).
 // Every wait is time-limited; on a timeout the CTA reports it, stops issuing,
 // lets its own copies and MMAs land, frees its tensor memory and returns.
 __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcArgs t, int64_t nitems, int nb,
@@ -432,40 +424,63 @@ __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcAr
     __syncwarp();
   } else {
     // ---------------- epilogue ----------------
+    // Warp 4 + q reads TMEM lanes 32q..32q+31 as two blocks of 16 lanes with the
+    // .16x256b shape: four lanes of the warp hold 8 consecutive outputs of one
+    // gathered column, so each 8-byte reduction of a warp covers 8 target rows x
+    // 32 contiguous bytes.
     const int quarter = warp & 3;
-    const int col = 32 * quarter + lane;
-    const uint32_t trow = tmem + ((uint32_t)(32 * quarter) << 16);
     int i = 0;
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x, ++i) {
       const int4 tile = a.tiles[it / nb];
       const int b = (int)(it % nb);
       const int n0 = TC_NMAX * b;
       const int n = min(TC_NMAX, 2 * a.M - n0);
-      float* out = nullptr;
-      float cs = 0.f;
-      if (col < tile.z * a.nrhs) {
-        const int2 pr = a.pairs[tile.y + col / a.nrhs];
-        const int k = col % a.nrhs;
-        cs = t.src_scale[(int64_t)pr.x * a.nrhs + k] * t.op_scale[tile.x];
-        out = (float*)(a.dst + ((int64_t)pr.y * a.nrhs + k) * a.dst_ld) + n0;
+      float* out[4];
+      float cs[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {   // columns 32q + 16 (h/2) + lane/4 + 8 (h%2)
+        const int col = 32 * quarter + 16 * (h >> 1) + (lane >> 2) + 8 * (h & 1);
+        out[h] = nullptr;
+        cs[h] = 0.f;
+        if (col < tile.z * a.nrhs) {
+          const int2 pr = a.pairs[tile.y + col / a.nrhs];
+          const int k = col % a.nrhs;
+          cs[h] = t.src_scale[(int64_t)pr.x * a.nrhs + k] * t.op_scale[tile.x];
+          out[h] = (float*)(a.dst + ((int64_t)pr.y * a.nrhs + k) * a.dst_ld) + n0 + 2 * (lane & 3);
+        }
       }
       int okw = 0;
       if (lane == 0) okw = mbar_wait(smem_u32(acc_full), (uint32_t)(i & 1), status) ? 1 : 0;
       okw = __shfl_sync(0xffffffffu, okw, 0);
       if (!okw) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      for (int j0 = 0; j0 < n; j0 += 16) {
-        float v[16], w[16];
-        tmem_ld16_pair(trow + (uint32_t)j0, trow + 256u + (uint32_t)j0, v, w);
-        if (out) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const float4 r = make_float4((v[4 * q] + w[4 * q]) * cs, (v[4 * q + 1] + w[4 * q + 1]) * cs,
-                                         (v[4 * q + 2] + w[4 * q + 2]) * cs, (v[4 * q + 3] + w[4 * q + 3]) * cs);
-            if (a.store)
-              *(float4*)(out + j0 + 4 * q) = r;
-            else
-              red_add4(out + j0 + 4 * q, r.x, r.y, r.z, r.w);
+      for (int blk = 0; blk < 2; ++blk) {
+        const uint32_t tb = tmem + ((uint32_t)(32 * quarter + 16 * blk) << 16);
+        float* oA = out[2 * blk];
+        float* oB = out[2 * blk + 1];
+        const float cA = cs[2 * blk], cB = cs[2 * blk + 1];
+        for (int j0 = 0; j0 < n; j0 += 32) {
+          uint32_t v[16], w[16];
+          tmem_ld16x256_x4(tb + (uint32_t)j0, v);
+          tmem_ld16x256_x4(tb + 256u + (uint32_t)j0, w);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int c = j0 + 8 * j;   // this thread's columns c + 2 (lane % 4) + {0, 1}
+            if (c < n) {
+              const float a0 = (__uint_as_float(v[4 * j]) + __uint_as_float(w[4 * j])) * cA;
+              const float a1 = (__uint_as_float(v[4 * j + 1]) + __uint_as_float(w[4 * j + 1])) * cA;
+              const float b0 = (__uint_as_float(v[4 * j + 2]) + __uint_as_float(w[4 * j + 2])) * cB;
+              const float b1 = (__uint_as_float(v[4 * j + 3]) + __uint_as_float(w[4 * j + 3])) * cB;
+              if (a.store) {
+                if (oA) *(float2*)(oA + c) = make_float2(a0, a1);
+                if (oB) *(float2*)(oB + c) = make_float2(b0, b1);
+              } else {
+                if (oA) red_add2(oA + c, a0, a1);
+                if (oB) red_add2(oB + c, b0, b1);
+              }
+            }
           }
         }
       }
