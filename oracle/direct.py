@@ -33,6 +33,53 @@ def direct(points: np.ndarray, f: np.ndarray, targets: np.ndarray | None = None,
     return out
 
 
+_WORKER = {}
+
+
+def _worker_init(points, f):
+    _WORKER["points"] = points
+    _WORKER["f"] = f
+
+
+def _worker_run(targets):
+    return direct(_WORKER["points"], _WORKER["f"], targets, chunk=8)
+
+
+class DirectPool:
+    """direct() on a sample of targets spread over `workers` processes (one per
+    host core): the same sums, split by target.  The processes are started with
+    `spawn` (safe after CUDA has been initialised in the parent) and keep the
+    points and densities; each runs single-threaded numpy."""
+
+    def __init__(self, points: np.ndarray, f: np.ndarray, workers: int):
+        import multiprocessing as mp
+        import os
+        self.workers = max(1, int(workers))
+        keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+        old = {k: os.environ.get(k) for k in keys}
+        for k in keys:
+            os.environ[k] = "1"
+        try:
+            self.pool = mp.get_context("spawn").Pool(
+                self.workers, initializer=_worker_init,
+                initargs=(np.ascontiguousarray(points), np.atleast_2d(np.asarray(f, dtype=np.complex128))))
+            self.pool.map(_worker_run, [np.zeros(0, dtype=np.int64)] * self.workers)   # started
+        finally:
+            for k, v in old.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def run(self, targets: np.ndarray) -> np.ndarray:
+        parts = [p for p in np.array_split(np.asarray(targets), self.workers) if p.size]
+        return np.concatenate(self.pool.map(_worker_run, parts), axis=1)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
 def direct_loop(points: np.ndarray, f: np.ndarray) -> np.ndarray:
     """Pure-Python double loop (tiny inputs only), for pinning direct()."""
     N = points.shape[0]

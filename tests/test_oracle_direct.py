@@ -51,3 +51,19 @@ def test_targets_subset_equals_full():
     f = rng.standard_normal((1, 500)) + 0j
     t = np.array([0, 17, 499, 250])
     assert np.allclose(direct(p, f, t), direct(p, f)[:, t], rtol=1e-14, atol=0)
+
+
+def test_process_pool_equals_single_process():
+    """The CPU baseline splits the targets over spawned processes: same sums."""
+    from oracle.direct import DirectPool
+    rng = np.random.default_rng(7)
+    p = rng.standard_normal((400, 3))
+    f = rng.standard_normal((2, 400)) + 1j * rng.standard_normal((2, 400))
+    t = rng.choice(400, 37, replace=False)
+    pool = DirectPool(p, f, 3)
+    try:
+        got = pool.run(t)
+    finally:
+        pool.close()
+    assert got.shape == (2, 37)
+    assert np.array_equal(got, direct(p, f, t, chunk=8))
