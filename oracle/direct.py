@@ -47,7 +47,8 @@ def _worker_run(targets):
 
 class DirectPool:
     """direct() on a sample of targets spread over `workers` processes (one per
-    host core): the same sums, split by target.  The processes are started with
+    host core): the same sums, split by target (equal up to the summation order
+    of the BLAS product).  The processes are started with
     `spawn` (safe after CUDA has been initialised in the parent) and keep the
     points and densities; each runs single-threaded numpy."""
 
