@@ -551,7 +551,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", default="auto", choices=["auto", "fp32", "tc"])
     ap.add_argument("--compare", action="store_true", help="also time the plain FP32 form and 16 RHS")
-    ap.add_argument("--requests", type=int, default=600, help="served8: requests in the stream")
+    ap.add_argument("--requests", type=int, default=2000, help="served8: requests in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="served8: Poisson arrival rate (1/s)")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="served8: the server's device arena")
     args = ap.parse_args()
