@@ -111,6 +111,20 @@ def traffic_for(kernel: str, source: str, workload: str):
     return None
 
 
+def max_over_ranks(x: float, dist=None, device="cuda") -> float:
+    """The largest x over the ranks of the process group (x itself on one rank)."""
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    if dist is not None and dist.is_initialized() and dist.get_world_size() > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Units per second of the whole job: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def cpu_oracle_sample(points, f, ntgt: int, seed: int, pool=None):
     """The oracle's direct sum (FP64 numpy) on ntgt targets: over the processes of
     `pool` (one per host core) if given, else in this process (one core)."""
@@ -207,6 +221,9 @@ def run_ours(args, wl):
         plan.apply(fd, ud)
     e1.record(stream)
     torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
     clocks = clk.stop()
     ms = e0.elapsed_time(e1) / args.steps
     # per-step latency distribution (separately, events around each step)
@@ -218,11 +235,8 @@ def run_ours(args, wl):
         b.synchronize()
         lat.append(a.elapsed_time(b))
     lat.sort()
-    tmax = torch.tensor([ms], device="cuda", dtype=torch.float64)
-    if dist:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    ms_max = float(tmax.item())
-    value = world * N * nrhs / (ms_max / 1e3)
+    ms_max = max_over_ranks(ms, dist)
+    value = whole_job_rate(N * nrhs, world, ms_max)
     # the same steps as one captured CUDA graph each (dfmm_graph_*)
     graph_ms = None
     if world == 1:
