@@ -365,6 +365,42 @@ def run_ours(args, wl):
         dist.destroy_process_group()
 
 
+def run_stage_errors(args, wl):
+    """Error that each translation family's FP16 split adds: one plan per family
+    with only that family on the tensor cores (options.tc_stages), against the
+    FP32 CUDA-core form of the same plan and against the FP64 direct sum."""
+    import numpy as np
+    import torch
+    import workloads
+    from oracle.direct import rel_err
+    from paper_1311_4257_gb300 import Plan
+    from paper_1311_4257_gb300 import build as B
+    B.build()
+    p = points_of(wl)
+    N = p.shape[0]
+    f = workloads.densities(N, 1, wl["seed"])
+    fd = torch.as_tensor(f.astype(np.complex64), device="cuda")
+    pool = oracle_pool(p, f)
+    t, ref, _ = cpu_oracle_sample(p, f, args.ref_targets or 1600, 1001, pool)
+    pool.close()
+    forms = [("fp32_cuda_cores", 1, 0), ("m2l_hf", 2, 1), ("m2l_lf", 2, 2), ("m2m", 2, 4), ("l2l", 2, 8),
+             ("p2l_proj", 2, 16), ("all_tensor_cores", 2, 31)]
+    out, u32 = {}, None
+    for name, mode, mask in forms:
+        plan = Plan(p, wl["K"], wl["eps"], cache_dir=args.cache_dir, m2l_mode=mode, tc_stages=mask)
+        u = plan.apply(fd)
+        torch.cuda.synchronize()
+        u = u.cpu().numpy().astype(np.complex128)
+        del plan
+        torch.cuda.empty_cache()
+        if u32 is None:
+            u32 = u
+        out[name] = {"vs_direct_sum_fp64": rel_err(u[:, t], ref), "vs_fp32_form": rel_err(u, u32)}
+    print(json.dumps({"metric": "relative error per translation family on the tensor cores (scaled FP16 hi/lo)",
+                      "workload": wl["desc"], "N": N, "eps": wl["eps"], "direct_sum_targets": int(len(t)),
+                      "stages": out}), flush=True)
+
+
 def _plain_rate(plans_pts, cache_dir, max_cols: int = 4):
     """Points x RHS per second of the plain form: FP32 CUDA-core plans, one
     right-hand side per apply, one apply at a time, over each geometry (at
@@ -568,6 +604,8 @@ def main():
     ap.add_argument("--requests", type=int, default=2000, help="served8: requests in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="served8: Poisson arrival rate (1/s)")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="served8: the server's device arena")
+    ap.add_argument("--stage-errors", action="store_true",
+                    help="instead of timing: the error each translation family's tensor-core split adds")
     args = ap.parse_args()
     os.makedirs(args.cache_dir, exist_ok=True)
     if args.workload in ("batch12", "served8", "solve_K64"):
@@ -578,6 +616,10 @@ def main():
             {"batch12": run_batch12, "served8": run_served8, "solve_K64": run_solve}[args.workload](args)
         return
     wl = WORKLOADS[args.workload]
+    if args.stage_errors:
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_stage_errors(args, wl)
+        return
     if args.impl == "reference":
         run_reference(args, wl)
     else:

@@ -64,6 +64,10 @@ typedef struct {
                               scaled FP16 hi/lo split; adds about 2e-6 relative error) */
   int32_t host_threads;    /* [0 = all cores] threads for the skeleton precompute */
   const char* cache_dir;   /* [NULL = no disk cache] directory for skeleton files */
+  int32_t tc_stages;       /* [0 = all] with m2l_mode 2, the translation families that run on
+                              the tensor cores, as a bit mask: 1 = HF M2L, 2 = LF M2L (V list),
+                              4 = M2M, 8 = L2L, 16 = P2L projection; the others run on the FP32
+                              CUDA cores.  For measuring the error each family's split adds. */
 } dfmm_options;
 
 /* Build a plan (Sec. 2.2 octree, lists, Eq. 2 representations and the

@@ -63,6 +63,9 @@ enum Fam { F_M2L_HF, F_M2L_LF, F_M2M, F_L2L, F_P2L_PROJ, F_P2M_EVAL, F_P2L_EVAL,
 const char* kFamName[F_COUNT] = {"m2l_hf", "m2l_lf", "m2m", "l2l", "p2l_proj", "p2m_eval",
                                  "p2l_eval", "l2p", "m2p", "p2p", "permute", "zero", "split"};
 
+// the translation families that m2l_mode 2 runs on the tensor cores (options.tc_stages)
+constexpr int kTcFamBit[F_COUNT] = {1, 2, 4, 8, 16, 0, 0, 0, 0, 0, 0, 0, 0};
+
 struct ProfRec {
   int fam;
   cudaEvent_t a, b;
@@ -1068,6 +1071,12 @@ Workspace* get_workspace(dfmm_plan_s* P, cudaStream_t s, int nrhs) {
 // (and the sources near them) and keep those rows in L2; blocks hold about
 // 8 MB of target rows.  Otherwise tiles stay in operator order, so that an
 // operator is read from DRAM once for all its tiles.
+// whether a translation stage runs on the tensor cores (m2l_mode 2, ranks padded
+// for the MMA, its family selected by options.tc_stages)
+bool on_tensor_cores(const dfmm_plan_s* P, const GemmPlan& g) {
+  return P->opt.m2l_mode == 2 && gemm_tc_supported(g.M, g.Kd) && (P->opt.tc_stages & kTcFamBit[g.fam]) != 0;
+}
+
 std::vector<int4> make_tiles(const GemmPlan& g, int nrhs, int cols) {
   const int per = std::max(1, cols / nrhs);
   std::vector<int4> t;
@@ -1125,7 +1134,7 @@ struct Runner {
   void gemm(const GemmPlan& g, const float2* src, int src_ld, int64_t src_rows, float2* dst, int dst_ld,
             int src_key, bool first = false) {
     if (g.npairs == 0) return;
-    const bool tc = P->opt.m2l_mode == 2 && gemm_tc_supported(g.M, g.Kd);
+    const bool tc = on_tensor_cores(P, g);
     const bool split = tc && (src_key < 0 || src_key != split_key);
     if (tc) split_key = src_key;
     if (count) { count[0] += split ? 2 : 1; return; }
@@ -1348,7 +1357,7 @@ size_t carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaS
   std::vector<int> tl_cols;
   for (const GemmPlan* g : all_gemms(P)) {
     if (g->npairs == 0) continue;
-    const int cols = (P->opt.m2l_mode == 2 && gemm_tc_supported(g->M, g->Kd)) ? gemm_tc_columns() : 64;
+    const int cols = on_tensor_cores(P, *g) ? gemm_tc_columns() : 64;
     tl_cols.push_back(cols);
     tl.push_back({g, make_tiles(*g, nrhs, cols)});
   }
@@ -1376,7 +1385,7 @@ int64_t workspace_bytes(dfmm_plan_s* P, int nrhs) {
 void build_images(dfmm_plan_s* P, cudaStream_t s) {
   for (const GemmPlan* gc : all_gemms(P)) {
     GemmPlan* g = const_cast<GemmPlan*>(gc);
-    if (g->npairs == 0 || g->nops == 0 || !gemm_tc_supported(g->M, g->Kd)) continue;
+    if (g->npairs == 0 || g->nops == 0 || !on_tensor_cores(P, *g)) continue;
     g->img = P->ar.alloc<__half>(tc_image_elems(g->M, g->Kd, g->nops));
     g->op_scale = P->ar.alloc<float>(g->nops);
     build_tc_image(g->ops, g->M, g->Kd, g->nops, g->img, g->op_scale, s);
@@ -1466,12 +1475,6 @@ int dfmm_plan(const double* points, int64_t N, double K, double eps, const dfmm_
     if (N < 1 || N > (int64_t)INT32_MAX / 2) return fail(DFMM_ERR_INVALID, "N must be in [1, 2^30]");
     if (!(K > 0) || K > 4096) return fail(DFMM_ERR_UNSUPPORTED, "K must be in (0, 4096]");
     if (!(eps >= 1e-8 && eps <= 1e-2)) return fail(DFMM_ERR_UNSUPPORTED, "eps must be in [1e-8, 1e-2]");
-    std::unique_ptr<dfmm_plan_s> P(new dfmm_plan_s());
-    DFMM_CUDA(cudaGetDevice(&P->device));
-    P->N = N;
-    P->K = K;
-    P->W = std::pow(2.0, std::max(0.0, std::ceil(std::log2(K))));
-    P->eps = eps;
     dfmm_options o{};
     if (opts) o = *opts;
     if (o.leaf_max <= 0) o.leaf_max = 64;
@@ -1484,6 +1487,14 @@ int dfmm_plan(const double* points, int64_t N, double K, double eps, const dfmm_
     // relative error, so it serves eps >= 1e-5; tighter tolerances use FP32
     // CUDA cores
     if (o.m2l_mode == 0) o.m2l_mode = eps >= 1e-5 ? 2 : 1;
+    if (o.tc_stages < 0 || o.tc_stages > 31) return fail(DFMM_ERR_INVALID, "tc_stages must be a mask in [0, 31]");
+    if (o.tc_stages == 0) o.tc_stages = 31;
+    std::unique_ptr<dfmm_plan_s> P(new dfmm_plan_s());
+    DFMM_CUDA(cudaGetDevice(&P->device));
+    P->N = N;
+    P->K = K;
+    P->W = std::pow(2.0, std::max(0.0, std::ceil(std::log2(K))));
+    P->eps = eps;
     P->opt = o;
     P->eps_op = eps * o.eps_op_factor;
     P->stats.N = N;

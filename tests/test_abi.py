@@ -40,6 +40,12 @@ def test_invalid_arguments_are_rejected_without_a_device(L):
     assert L.dfmm_plan(pts.ctypes.data, 0, 8.0, 1e-5, None, ctypes.byref(h)) == dfmm.ERR_INVALID
     assert L.dfmm_plan(pts.ctypes.data, 4, 8.0, 1.0, None, ctypes.byref(h)) == dfmm.ERR_UNSUPPORTED
     assert L.dfmm_plan(pts.ctypes.data, 4, -1.0, 1e-5, None, ctypes.byref(h)) == dfmm.ERR_UNSUPPORTED
+    # options are checked before any device call
+    o = dfmm.Options(0, 0, 0, 0, 0.0, 3, 0, None, 0)
+    assert L.dfmm_plan(pts.ctypes.data, 4, 8.0, 1e-5, ctypes.byref(o), ctypes.byref(h)) == dfmm.ERR_INVALID
+    o = dfmm.Options(0, 0, 0, 0, 0.0, 2, 0, None, 32)
+    assert L.dfmm_plan(pts.ctypes.data, 4, 8.0, 1e-5, ctypes.byref(o), ctypes.byref(h)) == dfmm.ERR_INVALID
+    assert b"tc_stages" in L.dfmm_last_error()
     assert L.dfmm_apply(None, None, None, 1, None) == dfmm.ERR_INVALID
     assert b"null" in L.dfmm_last_error()
     # batched apply: an empty batch is a no-op; missing arrays are rejected

@@ -205,3 +205,22 @@ def test_tensor_core_form_matches_cuda_core_form(nrhs):
     assert OD.rel_err(u_tc, u_fp) < 5e-6
     t = np.arange(0, p.shape[0], 7)
     assert OD.rel_err(u_tc[:, t], OD.direct(p, f, t)) < 1e-5
+
+
+@pytest.mark.gpu
+def test_tensor_core_families_one_at_a_time():
+    """options.tc_stages puts one translation family on the tensor cores: each adds
+    less error than all of them together, and a mask of every family is the
+    default tensor-core form."""
+    p = workloads.sphere(8.0, 0)
+    f = workloads.densities(p.shape[0], 1, 5)
+    u_fp = _apply(_plan(p, 8.0, 1e-5, m2l_mode=1), f)
+    u_all = _apply(_plan(p, 8.0, 1e-5, m2l_mode=2), f)
+    e_all = OD.rel_err(u_all, u_fp)
+    assert 0 < e_all < 5e-6
+    assert OD.rel_err(_apply(_plan(p, 8.0, 1e-5, m2l_mode=2, tc_stages=31), f), u_all) < 1e-6
+    for mask in (1, 2, 4, 8):
+        e = OD.rel_err(_apply(_plan(p, 8.0, 1e-5, m2l_mode=2, tc_stages=mask), f), u_fp)
+        assert 0 < e < e_all * 1.2 + 1e-7, (mask, e, e_all)
+    # P2L projection (X lists, only where the LF tree is adaptive) alone
+    assert OD.rel_err(_apply(_plan(p, 8.0, 1e-5, m2l_mode=2, tc_stages=16), f), u_fp) < e_all * 1.2 + 1e-7
