@@ -1,6 +1,6 @@
 // Apply-time kernels of the directional FMM matvec (FP32).
 //
-//  * gemm_stage_kernel: every translation of Alg. 1 (P2M/P2L projections,
+//  * gemm_stage_kernel: every translation of Alg. 1 (P2L projection,
 //    LF/HF-M2M, HF-M2L, LF-M2L, HF/LF-L2L) is "y[dst] += T_op x[src]" over a
 //    list of (src, dst) pairs grouped by operator.  One CTA computes a
 //    64-row x 64-column block of T_op X, where the columns are the gathered
@@ -8,10 +8,12 @@
 //    into the target states with vector atomics (targets of one operator are
 //    distinct, different operators meet in L2).  This is the plain CUDA-core
 //    form; the tensor-core form is in m2l_tc.cu.
-//  * p2c_kernel: potentials at check points from points (P2M, P2L), with the
-//    phase 2 pi |x - y| reduced in a compensated form so that far check
+//  * p2c_kernel: potentials at check points from points (P2L, X lists), with
+//    the phase 2 pi |x - y| reduced in a compensated form so that far check
 //    points keep full FP32 accuracy.
-//  * rows_kernel: L2P and M2P through precomputed rows.
+//  * p2m_rows_kernel: P2M as a sum of FP64-formed per-point rows.
+//  * l2p_kernel: L2P through precomputed per-point rows (flat row stream).
+//  * rows_kernel: M2P (W lists) through precomputed rows.
 //  * p2p_kernel: the near field (U lists) in FP32 on box-local coordinates.
 #include "apply.h"
 
@@ -139,8 +141,8 @@ constexpr int P2C_THREADS = 256;
 constexpr int P2C_CHUNK = 128;
 constexpr int P2C_JOBS = 8;   // rounds of side-by-side jobs per block
 
-// Check-point potentials of leaf points (the sample of Eq. 6 that P2M and P2L
-// project).  A group of tpj threads (one per check point) takes one job; a
+// Check-point potentials of leaf points (the sample of Eq. 6 that P2L
+// projects).  A group of tpj threads (one per check point) takes one job; a
 // block runs P2C_THREADS / tpj groups side by side, P2C_JOBS rounds in a row,
 // and keeps its check points in registers across the rounds.  NR right-hand
 // sides are accumulated per pass.
