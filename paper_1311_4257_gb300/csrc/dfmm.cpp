@@ -121,6 +121,9 @@ struct Workspace {
   float* ascale = nullptr;                              // its per-row scales
   std::vector<float2*> S, T;                            // per level (LF or HF states)
   std::vector<std::pair<void*, size_t>> zero;           // reset before each apply
+  std::vector<std::pair<void*, size_t>> zero_late;      // reset on the side stream, first read by HF M2M
+  cudaStream_t side = nullptr;                          // for zero_late, beside P2M and the V list
+  cudaEvent_t fork = nullptr, join = nullptr;
   std::map<std::pair<const void*, int>, std::pair<int4*, int64_t>> tiles;   // key (stage, nrhs * 1024 + columns)
   float2 *f_dev = nullptr, *u_dev = nullptr;            // staging for host applies
   unsigned* status = nullptr;
@@ -130,6 +133,9 @@ struct Workspace {
   size_t pool_used = 0;
   ~Workspace() {
     for (auto e : pool) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    if (join) cudaEventDestroy(join);
+    if (side) cudaStreamDestroy(side);
   }
   cudaEvent_t ev() {
     if (pool_used == pool.size()) {
@@ -1040,8 +1046,8 @@ Workspace* get_workspace(dfmm_plan_s* P, cudaStream_t s, int nrhs) {
     else if (P->l_top >= 0 && l >= P->l_top) {
       R = P->hf[l].R;
       int64_t so = (int64_t)P->hf[l].out_keys.size(), si = (int64_t)P->hf[l].in_keys.size();
-      if (so) { W->S[l] = ar.alloc<float2>(so * nrhs * R); W->zero.push_back({W->S[l], (size_t)so * nrhs * R * 8}); }
-      if (si) { W->T[l] = ar.alloc<float2>(si * nrhs * R); W->zero.push_back({W->T[l], (size_t)si * nrhs * R * 8}); }
+      if (so) { W->S[l] = ar.alloc<float2>(so * nrhs * R); W->zero_late.push_back({W->S[l], (size_t)so * nrhs * R * 8}); }
+      if (si) { W->T[l] = ar.alloc<float2>(si * nrhs * R); W->zero_late.push_back({W->T[l], (size_t)si * nrhs * R * 8}); }
       continue;
     } else continue;
     W->S[l] = ar.alloc<float2>(rows * nrhs * R);
@@ -1177,6 +1183,18 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
   const int nl = P->nl;
   auto S = [&](int l) { return count ? (float2*)nullptr : W->S[l]; };
   auto T = [&](int l) { return count ? (float2*)nullptr : W->T[l]; };
+  const bool late = !count && !W->zero_late.empty();
+  if (late) {   // HF states: reset on a side stream while P2M and the V list run
+    if (!W->side) {
+      DFMM_CUDA(cudaStreamCreateWithFlags(&W->side, cudaStreamNonBlocking));
+      DFMM_CUDA(cudaEventCreateWithFlags(&W->fork, cudaEventDisableTiming));
+      DFMM_CUDA(cudaEventCreateWithFlags(&W->join, cudaEventDisableTiming));
+    }
+    DFMM_CUDA(cudaEventRecord(W->fork, s));
+    DFMM_CUDA(cudaStreamWaitEvent(W->side, W->fork, 0));
+    for (auto& z : W->zero_late) DFMM_CUDA(cudaMemsetAsync(z.first, 0, z.second, W->side));
+    DFMM_CUDA(cudaEventRecord(W->join, W->side));
+  }
   if (!count) {
     ProfScope ps(W, s, F_ZERO, 0.0, 0.0);
     for (auto& z : W->zero) DFMM_CUDA(cudaMemsetAsync(z.first, 0, z.second, s));
@@ -1207,6 +1225,7 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
   if (P->l_lf0 < nl)
     R.gemm(P->lf[P->l_lf0].v, S(P->l_lf0), P->lf[P->l_lf0].R, P->lf[P->l_lf0].nbox, T(P->l_lf0),
            P->lf[P->l_lf0].R, kSrcS + P->l_lf0);
+  if (late) DFMM_CUDA(cudaStreamWaitEvent(s, W->join, 0));   // the HF states are reset
   // 2. HF upward: M2M, then that level's M2L
   if (P->l_top >= 0) {
     for (int l = P->l1; l >= P->l_top; --l) {
