@@ -101,7 +101,7 @@ def test_small_sphere_parity():
     assert e_fmm <= 1e-5 and e_dir <= 1e-4
 
 
-def test_config1_sphere_k8_eps1e6():
+def test_sphere_k8_eps1e6():
     """Sphere diameter 8, N = 20,106, eps = 1e-6, all targets of the direct sum."""
     p = workloads.sphere(8.0, 0)
     e_fmm, e_dir, e_or = _parity(p, 8.0, 1e-6, ntgt=4000)
@@ -167,7 +167,7 @@ def test_points_outside_domain_rejected():
     assert e.value.code == -2
 
 
-def test_config2_sphere_k64_sampled_targets():
+def test_sphere_k64_sampled_targets():
     """Sphere diameter 64, N = 1,286,796 (the benchmarked workload): sampled
     targets against the direct sum of Eq. 1, eps = 1e-5."""
     import torch
@@ -181,7 +181,7 @@ def test_config2_sphere_k64_sampled_targets():
     assert OD.rel_err(u[:, t], ud) <= 1e-5
 
 
-def test_config3_ellipsoid_k128_sampled_targets():
+def test_ellipsoid_k128_sampled_targets():
     """Ellipsoid with semi-axes (64, 32, 16), K = 128, N = 1,625,002 (seed 2),
     eps 1e-5, tensor-core form: 200 sampled targets against the direct sum of
     Eq. 1, and the tensor-core result against the FP32 form on all targets."""

@@ -127,7 +127,7 @@ def test_adaptive_tree_with_w_and_x_lists():
 
 
 @pytest.mark.slow
-def test_config1_sphere_k8_against_direct_sum():
+def test_sphere_k8_against_direct_sum():
     """Sphere of diameter 8, N = 20,106 (seed 0): FMM within eps of Eq. 1."""
     p = workloads.sphere(8.0, 0)
     assert p.shape[0] == 20106
