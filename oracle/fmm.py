@@ -14,11 +14,13 @@ Passes, in the order of Alg. 1 (Sec. 2.3):
      LF-L2L into children; at leaves L2P and M2P over the W list.
   5. Near field (not written in Alg. 1, implied by Eq. 1): P2P over U lists.
 
-Representations and operators are those of oracle.skeleton (least-squares
-form of Eq. 2).  Every operator is grouped by its key (direction, octant or
-offset) and applied with numpy matmul to the stacked states of its boxes.
-With fp32=True the operators and the states are rounded to complex64 and the
-translations run in complex64, to estimate the effect of single precision.
+Representations and operators are those of oracle.skeleton: by default the
+least-squares form of Eq. 2 (form="ls"), or with form="plain" the paper's own
+form, equivalent charges D u on the r check points with D = G(a, b)^{-1}.
+Every operator is grouped by its key (direction, octant or offset) and
+applied with numpy matmul to the stacked states of its boxes.  With fp32=True
+the operators and the states are rounded to complex64 and the translations
+run in complex64, to estimate the effect of single precision.
 """
 from __future__ import annotations
 
@@ -86,6 +88,29 @@ class Plan:
         return self.reps.hf(self.tree.levels[l].w, cell).r
 
 
+# Translation operators (Alg. 1), each from the relative position of the two
+# boxes alone (translation invariance, Sec. 2.2); every one maps the source
+# box's state to the target box's state.
+
+def m2m_operator(rep_parent, rep_child, delta: np.ndarray) -> np.ndarray:
+    """Child outgoing state -> parent outgoing state; delta = c_child - c_parent.
+    The child's field at the parent's check points (parent frame a2, i.e.
+    a2 - delta in the child frame), projected by the parent."""
+    return rep_parent.p_out() @ rep_child.phi(rep_parent.a2 - delta)
+
+
+def m2l_operator(rep_tgt, rep_src, delta: np.ndarray) -> np.ndarray:
+    """Source outgoing state -> target incoming state; delta = c_src - c_tgt.
+    The source's field at the target's box check points."""
+    return rep_tgt.p_in() @ rep_src.phi(rep_tgt.b2 - delta)
+
+
+def l2l_operator(rep_child, rep_parent, delta: np.ndarray) -> np.ndarray:
+    """Parent incoming state -> child incoming state; delta = c_child - c_parent.
+    The parent's incoming field at the child's box check points."""
+    return rep_child.p_in() @ rep_parent.psi(rep_child.b2 + delta)
+
+
 def _mm(op, x, fp32):
     """op (r_t, r_s) applied to x (n, nrhs, r_s) -> (n, nrhs, r_t)."""
     if fp32:
@@ -97,15 +122,31 @@ def _rnd(x, fp32):
     return x.astype(np.complex64).astype(np.complex128) if fp32 else x
 
 
-def fmm(plan: Plan, f: np.ndarray, fp32: bool = False) -> np.ndarray:
-    """Potentials (nrhs, N) in the caller's point order for densities f (nrhs, N)."""
+class _PlainForm:
+    """The plan's representations in the paper's form of Eq. 2."""
+
+    def __init__(self, reps: sk.RepSet):
+        self.reps = reps
+
+    def hf(self, w: float, cell: int):
+        return self.reps.hf(w, cell).plain()
+
+    def lf(self, w: float):
+        return self.reps.lf(w).plain()
+
+
+def fmm(plan: Plan, f: np.ndarray, fp32: bool = False, form: str = "ls") -> np.ndarray:
+    """Potentials (nrhs, N) in the caller's point order for densities f (nrhs, N).
+    form: "ls" (least-squares form of Eq. 2) or "plain" (D = G(a, b)^{-1})."""
     T = plan.tree
     f = np.atleast_2d(np.asarray(f, dtype=np.complex128))
     nrhs = f.shape[0]
     fs = f[:, T.perm].T.copy()                   # (N, nrhs), Morton order
     ys = plan.ys
     levels = T.levels
-    reps = plan.reps
+    if form not in ("ls", "plain"):
+        raise ValueError("form must be 'ls' or 'plain'")
+    reps = plan.reps if form == "ls" else _PlainForm(plan.reps)
     C = plan.centers
 
     # ---------------------------------------------------- 1. LF upward ---
@@ -123,7 +164,7 @@ def fmm(plan: Plan, f: np.ndarray, fp32: bool = False) -> np.ndarray:
             Lc = levels[L.l + 1]
             rc = reps.lf(Lc.w)
             for o in range(8):
-                op = Pout @ rc.phi(rep.a2 - octant_offset(o, Lc.w))
+                op = m2m_operator(rep, rc, octant_offset(o, Lc.w))
                 par = Lc.parent
                 oc = _octant_of(Lc.coords)
                 sel = np.nonzero(oc == o)[0]
@@ -144,7 +185,6 @@ def fmm(plan: Plan, f: np.ndarray, fp32: bool = False) -> np.ndarray:
         oc = _octant_of(Lc.coords)
         for d in np.unique(dirs):
             rep = reps.hf(L.w, d)
-            Pout = rep.p_out()
             slots = np.nonzero(dirs == d)[0]
             pb = box[slots]
             for k in range(8):
@@ -165,7 +205,7 @@ def fmm(plan: Plan, f: np.ndarray, fp32: bool = False) -> np.ndarray:
                         ckeys = ch[so] * ndc + cd
                         pos = np.searchsorted(plan.act[l + 1][0], ckeys)
                         src = S_hf[l + 1][pos][:, :, :rc.r]
-                    op = Pout @ rc.phi(rep.a2 - octant_offset(int(o), Lc.w))
+                    op = m2m_operator(rep, rc, octant_offset(int(o), Lc.w))
                     S[sl[so], :, :rep.r] += _mm(op, src, fp32)
         S_hf[l] = _rnd(S, fp32)
 
@@ -197,7 +237,7 @@ def fmm(plan: Plan, f: np.ndarray, fp32: bool = False) -> np.ndarray:
                     sl = slots[has]
                     for o in np.unique(oc[ch]):
                         so = oc[ch] == o
-                        op = rc.p_in() @ rp.psi(rc.b2 + octant_offset(int(o), L.w))
+                        op = l2l_operator(rc, rp, octant_offset(int(o), L.w))
                         pos = np.searchsorted(keys, ch[so] * nd + cd)
                         np.add.at(Tin, (pos, slice(None), slice(0, rc.r)),
                                   _mm(op, T_hf[l - 1][sl[so]][:, :, :rp.r], fp32))
@@ -215,7 +255,7 @@ def fmm(plan: Plan, f: np.ndarray, fp32: bool = False) -> np.ndarray:
                 din, dout = int(p.dir_in[idx[0]]), int(p.dir_out[idx[0]])
                 rb = reps.hf(L.w, din)
                 ra = reps.hf(L.w, dout)
-                op = rb.p_in() @ ra.phi(rb.b2 - L.w * m)
+                op = m2l_operator(rb, ra, L.w * m)
                 spos = np.searchsorted(okeys, p.src[idx] * nd + dout)
                 tpos = np.searchsorted(keys, p.tgt[idx] * nd + din)
                 np.add.at(Tin, (tpos, slice(None), slice(0, rb.r)),
@@ -244,7 +284,7 @@ def fmm(plan: Plan, f: np.ndarray, fp32: bool = False) -> np.ndarray:
                     sl = slots[has]
                     for o in np.unique(oc[ch]):
                         so = oc[ch] == o
-                        op = rep.p_in() @ rp.psi(rep.b2 + octant_offset(int(o), L.w))
+                        op = l2l_operator(rep, rp, octant_offset(int(o), L.w))
                         np.add.at(Tin, ch[so], _mm(op, T_hf[L.l - 1][sl[so]][:, :, :rp.r], fp32))
         else:
             # LF-L2L from the LF parent
@@ -252,7 +292,7 @@ def fmm(plan: Plan, f: np.ndarray, fp32: bool = False) -> np.ndarray:
             for o in range(8):
                 sel = np.nonzero(oc == o)[0]
                 if sel.size:
-                    op = rep.p_in() @ rp.psi(rep.b2 + octant_offset(o, L.w))
+                    op = l2l_operator(rep, rp, octant_offset(o, L.w))
                     Tin[sel] += _mm(op, T_lf[Lp.l][L.parent[sel]], fp32)
         # LF-M2L over the V list
         tgt, src, m = plan.lf.V.get(L.l, (np.zeros(0, np.int64),) * 2 + (np.zeros((0, 3), np.int64),))
@@ -260,7 +300,7 @@ def fmm(plan: Plan, f: np.ndarray, fp32: bool = False) -> np.ndarray:
             mk = (m[:, 0] + 3) * 49 + (m[:, 1] + 3) * 7 + (m[:, 2] + 3)
             for key in np.unique(mk):
                 sel = np.nonzero(mk == key)[0]
-                op = rep.p_in() @ rep.phi(rep.b2 - L.w * m[sel[0]])
+                op = m2l_operator(rep, rep, L.w * m[sel[0]])
                 np.add.at(Tin, tgt[sel], _mm(op, S_lf[L.l][src[sel]], fp32))
         # P2L over the X list (targets at this level)
         X = plan.lf.X

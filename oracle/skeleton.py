@@ -19,7 +19,9 @@ Engquist-Ying 2010, which is not available).  The reading implemented here:
   3. Two rounds of column-pivoted QR on the transpose of the weighted
      G(X_s, b) pick 2r far check points a2; the first r are the incoming
      equivalent points (reciprocity, G(x, y) = G(y, x)).
-  4. D of Eq. 2 is applied in least-squares form over the 2r check points,
+  4. D of Eq. 2 is applied in least-squares form over the 2r check points
+     (PlainRep below is the paper's own form, D = G(a, b)^{-1}, on the same
+     skeleton; the FMM runs on either),
      and the equivalent charges are carried in the basis that is orthonormal
      on the weighted check points:  with  W G(a2, b) = Q_o R_o,
          outgoing state  s = Q_o^H W u(a2)        (u = check potentials),
@@ -355,6 +357,54 @@ class Rep:
     def mapped(self, sym, cell: int) -> "Rep":
         return Rep(self.w, cell, self.r, apply_sym(sym, self.b2), apply_sym(sym, self.a2),
                    self.Wa2, self.Qo, self.Ro_inv, self.Qi, self.Ri_inv)
+
+    def plain(self) -> "PlainRep":
+        """The same skeleton in the paper's own form of Eq. 2 (cached)."""
+        if getattr(self, "_plain", None) is None:
+            self._plain = PlainRep(self)
+        return self._plain
+
+
+class PlainRep:
+    """Eq. 2 exactly as Sec. 2.1 states it, on the skeleton of a Rep:
+    r equivalent points b = b2[:r] in the box and r check points a = a2[:r]
+    in the far region, with the translation matrix D = G(a, b)^{-1}.
+
+    Outgoing: the check potentials u(a) = sum_i G(a, y_i) f_i of the box's
+    sources give the equivalent charges f_b = D u(a), whose field at a far x
+    is G(x, b) f_b.  Incoming (the mirror image, reciprocity G(x, y) = G(y, x)):
+    far equivalent points a with charges g = D_in v(b), D_in = G(b, a)^{-1},
+    from the check potentials v(b) of the far sources; their field at y in the
+    box is G(y, a) g.
+
+    Same interface as Rep (p_out, phi, p_in, psi; the check-point matrices
+    take all 2r check points and use the first r), so the FMM passes run
+    unchanged on either form."""
+
+    def __init__(self, rep: Rep):
+        self.w, self.cell, self.r = rep.w, rep.cell, rep.r
+        self.b2, self.a2 = rep.b2, rep.a2
+        r = rep.r
+        self.b = rep.b2[:r]
+        self.a = rep.a2[:r]
+        self.D_out = np.linalg.inv(G(self.a, self.b))
+        self.D_in = np.linalg.inv(G(self.b, self.a))
+
+    def p_out(self) -> np.ndarray:
+        """Check potentials at a2 -> equivalent charges D u(a): (r, 2r)."""
+        return np.hstack([self.D_out, np.zeros((self.r, self.r), np.complex128)])
+
+    def phi(self, x: np.ndarray) -> np.ndarray:
+        """Field at x of unit equivalent charges at b: (m, r)."""
+        return G(x, self.b)
+
+    def p_in(self) -> np.ndarray:
+        """Check potentials at b2 -> incoming equivalent charges D_in v(b): (r, 2r)."""
+        return np.hstack([self.D_in, np.zeros((self.r, self.r), np.complex128)])
+
+    def psi(self, y: np.ndarray) -> np.ndarray:
+        """Field at y (in the box) of unit equivalent charges at a: (m, r)."""
+        return G(y, self.a)
 
 
 def box_samples_mixed(st: Stream, w: float, S: int) -> np.ndarray:

@@ -10,6 +10,7 @@ import pytest
 
 import workloads
 from oracle import fmm as F
+from oracle import octree as ot
 from oracle import skeleton as S
 from oracle.direct import direct, rel_err
 from oracle.kernel import G
@@ -75,10 +76,132 @@ def test_separation_ranks_near_table1():
     gold = json.load(open(os.path.join(GOLD, "table1_separation_rank.json")))
     for eps_key in ("1e-4", "1e-6"):
         eps = float(eps_key)
-        for k, w in enumerate((1.0, 2.0)):
-            r = S.hf_rep(w, 0, 4.0, S.SkelParams(eps_op=eps)).r
+        for k, w in enumerate((1.0, 2.0, 4.0, 8.0)):
+            assert gold["widths"][k] == w
+            r = S.hf_rep(w, 0, max(4.0, w), S.SkelParams(eps_op=eps)).r
             ref = gold["rank"][eps_key][k]
             assert 0.5 * ref <= r <= 2.0 * ref, (eps, w, r, ref)
+
+
+@pytest.mark.parametrize("kind", ["hf", "lf"])
+def test_plain_eq2_on_fresh_samples(kind):
+    """Eq. 2 as printed, G(x, y) ~ G(x, b) D G(a, y) with D = G(a, b)^{-1} on the
+    r skeleton points, reproduces the kernel on fresh sources and targets of
+    the representation's region (outgoing and, by reciprocity, incoming)."""
+    prm = S.SkelParams(eps_op=1e-5)
+    st = S.Stream(2025)
+    if kind == "hf":
+        rep = S.hf_rep(2.0, 0, 4.0, prm)
+        X = S.region_hf(st, 2.0, 0, 4.0, 600)
+        Y = S.box_samples(st, 2.0, 300)
+    else:
+        rep = S.lf_rep(0.5, 2.0, prm)
+        X = S.region_lf(st, 0.5, 2.0, 600)
+        Y = S.box_samples(st, 0.5, 300)
+    pr = rep.plain()
+    assert pr.b.shape == (rep.r, 3) and pr.a.shape == (rep.r, 3)
+    assert np.allclose(pr.D_out @ G(pr.a, pr.b), np.eye(rep.r), atol=1e-6)
+    wt = np.linalg.norm(X, axis=1)[:, None]
+    exact = G(X, Y)
+    out = G(X, pr.b) @ pr.D_out @ G(pr.a, Y)
+    assert np.linalg.norm(wt * (exact - out)) / np.linalg.norm(wt * exact) < 20 * prm.eps_op
+    inc = G(Y, pr.a) @ pr.D_in @ G(pr.b, X)
+    assert np.linalg.norm(wt.T * (exact.T - inc)) / np.linalg.norm(wt.T * exact.T) < 20 * prm.eps_op
+    # the interface the FMM passes use: state = p_out u(a2), field = phi(x) state
+    # (another association order: D has a condition number of about 1 / eps_op)
+    assert np.allclose(pr.phi(X) @ (pr.p_out() @ G(rep.a2, Y)), out, rtol=0, atol=1e-8 * np.abs(out).max())
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-5, 1e-6])
+def test_plain_and_least_squares_forms_agree(eps):
+    """The FMM with the paper's form of Eq. 2 (D = G(a, b)^{-1}) and with the
+    least-squares form on the same skeletons: each within eps of the direct
+    sum of Eq. 1 on all targets, and within eps of each other."""
+    p = workloads.sphere(4.0, 5)
+    f = workloads.densities(p.shape[0], 1, 5)
+    plan = F.Plan(p, 4.0, F.FMMParams(eps=eps))
+    ref = direct(p, f)
+    u_ls = F.fmm(plan, f)
+    u_plain = F.fmm(plan, f, form="plain")
+    assert rel_err(u_ls, ref) <= eps
+    assert rel_err(u_plain, ref) <= eps
+    assert rel_err(u_plain, u_ls) <= eps
+
+
+@pytest.mark.slow
+def test_plain_form_sphere_k8():
+    """Sphere of diameter 8, N = 20,106: the paper's form of Eq. 2 within eps of
+    the direct sum on 1000 sampled targets, and of the least-squares form."""
+    p = workloads.sphere(8.0, 0)
+    f = workloads.densities(p.shape[0], 1, 0)
+    plan = F.Plan(p, 8.0, F.FMMParams(eps=1e-5))
+    t = np.random.default_rng(1000).choice(p.shape[0], 1000, replace=False)
+    ref = direct(p, f, t)
+    u_plain = F.fmm(plan, f, form="plain")
+    assert rel_err(u_plain[:, t], ref) <= 1e-5
+    assert rel_err(u_plain, F.fmm(plan, f)) <= 1e-5
+
+
+def _operator_from_absolute_points(rep_t, rep_s, c_t, c_s, kind):
+    """A translation operator evaluated on the two boxes' skeleton points placed
+    at their absolute positions (no relative offset is formed anywhere)."""
+    if kind == "m2m":     # child (s) outgoing -> parent (t) outgoing
+        return rep_t.p_out() @ (G(c_t + rep_t.a2, c_s + rep_s.b) @ rep_s.Ro_inv)
+    if kind == "m2l":     # source (s) outgoing -> target (t) incoming
+        return rep_t.p_in() @ (G(c_t + rep_t.b2, c_s + rep_s.b) @ rep_s.Ro_inv)
+    # l2l: parent (s) incoming -> child (t) incoming
+    return rep_t.p_in() @ ((G(c_t + rep_t.b2, c_s + rep_s.a_in) * rep_s.Wa2[None, :rep_s.r]) @ rep_s.Ri_inv)
+
+
+def test_translation_invariance_of_the_operators():
+    """P7 (Sec. 2.2: the operators depend only on the relative position of the
+    boxes): the M2M, M2L and L2L operators the FMM forms from an offset equal
+    the same maps evaluated between the skeletons placed at the boxes' absolute
+    centres, for real box pairs of a sphere's tree.  The kernel blocks agree to
+    1e-13; the operators to 1e-9, because their factors (R^{-1}, condition
+    number about 1 / eps_op) amplify the rounding of the absolute coordinates
+    (a wrong offset or sign changes them at order one)."""
+    p = workloads.sphere(8.0, 3, n=4000)
+    plan = F.Plan(p, 8.0, F.FMMParams(eps=1e-4))
+    T = plan.tree
+    C = plan.centers
+    rs = plan.reps
+    checked = 0
+    for h in plan.hf:
+        L = T.levels[h.l]
+        for q in range(0, h.tgt.size, max(1, h.tgt.size // 5)):
+            rb, ra = rs.hf(L.w, int(h.dir_in[q])), rs.hf(L.w, int(h.dir_out[q]))
+            op = F.m2l_operator(rb, ra, L.w * h.m[q])
+            ref = _operator_from_absolute_points(rb, ra, C[h.l][h.tgt[q]], C[h.l][h.src[q]], "m2l")
+            assert np.abs(op - ref).max() <= 1e-9 * np.abs(ref).max()
+            kb = G(rb.b2 - L.w * h.m[q], ra.b)
+            kb_abs = G(C[h.l][h.tgt[q]] + rb.b2, C[h.l][h.src[q]] + ra.b)
+            assert np.abs(kb - kb_abs).max() <= 1e-13 * np.abs(kb_abs).max()
+            checked += 1
+    for l in range(plan.l_top + 1, plan.l1 + 1):
+        L, P = T.levels[l], T.levels[l - 1]
+        for c in range(0, L.n, max(1, L.n // 5)):
+            pb = L.parent[c]
+            d_child = int(ot.direction(np.array([[1, 0, 0]]), ot.n_cells(L.w))[0])
+            d_par = int(np.nonzero(ot.parent_direction(np.arange(ot.n_directions(P.w)), ot.n_cells(P.w))
+                                   == d_child)[0][0])
+            rc, rp = rs.hf(L.w, d_child), rs.hf(P.w, d_par)
+            delta = C[l][c] - C[l - 1][pb]
+            op = F.m2m_operator(rp, rc, delta)
+            ref = _operator_from_absolute_points(rp, rc, C[l - 1][pb], C[l][c], "m2m")
+            assert np.abs(op - ref).max() <= 1e-9 * np.abs(ref).max()
+            op = F.l2l_operator(rc, rp, delta)
+            ref = _operator_from_absolute_points(rc, rp, C[l][c], C[l - 1][pb], "l2l")
+            assert np.abs(op - ref).max() <= 1e-9 * np.abs(ref).max()
+            checked += 2
+    for l, (tg, sr, m) in plan.lf.V.items():
+        rep = rs.lf(T.levels[l].w)
+        for q in range(0, tg.size, max(1, tg.size // 5)):
+            op = F.m2l_operator(rep, rep, T.levels[l].w * m[q])
+            ref = _operator_from_absolute_points(rep, rep, C[l][tg[q]], C[l][sr[q]], "m2l")
+            assert np.abs(op - ref).max() <= 1e-9 * np.abs(ref).max()
+            checked += 1
+    assert checked > 20
 
 
 def test_single_precision_translations_stay_within_tolerance():
@@ -136,3 +259,51 @@ def test_sphere_k8_against_direct_sum():
     t = np.random.default_rng(1000).choice(p.shape[0], 1000, replace=False)
     e = rel_err(F.fmm(plan, f)[:, t], direct(p, f, t))
     assert e <= 1e-5
+
+
+def test_pivoted_qr_matches_lapack():
+    """The oracle's column-pivoted Householder QR picks the same columns, in the
+    same order and with the same |R_kk|, as LAPACK's pivoted QR (zgeqp3 through
+    scipy) on matrices without near-ties, tall and wide."""
+    sl = pytest.importorskip("scipy.linalg")
+    rng = np.random.default_rng(11)
+    for m, n in ((40, 30), (30, 60)):
+        A = rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))
+        A = A * np.exp(rng.uniform(-3, 3, n))[None, :]        # columns of uneven size
+        piv, diag = S.pivoted_qr_pivots(A, 0.0)
+        _, R, P = sl.qr(A, pivoting=True, mode="economic")
+        k = min(m, n)
+        assert piv == P[:k].tolist()
+        assert np.allclose(diag, np.abs(np.diag(R))[:k], rtol=1e-10)
+    # the tolerance stops at the first |R_kk| <= tol |R_00|
+    B = rng.standard_normal((50, 8)) @ rng.standard_normal((8, 40))
+    piv, diag = S.pivoted_qr_pivots(B, 1e-8)
+    assert len(piv) == 8 and all(d > 1e-8 * diag[0] for d in diag)
+
+
+def test_sketch_and_sample_streams_are_random_like():
+    """The counter-based SplitMix64 streams: the sketch matrix is +-1, balanced
+    and nearly orthogonal across rows; uniform draws pass a Kolmogorov-Smirnov
+    test and consecutive draws are uncorrelated (a Weyl sequence without the
+    mixing function fails the last check); the sketch's entry k is the sign of
+    the k-th draw of the same stream."""
+    scs = pytest.importorskip("scipy.stats")
+    R = S.rademacher(12345, 64, 4096)
+    assert set(np.unique(R).tolist()) == {-1.0, 1.0}
+    assert np.abs(R.mean(axis=1)).max() < 5 / np.sqrt(4096)
+    Gm = R @ R.T / 4096
+    assert np.abs(Gm - np.eye(64)).max() < 6 / np.sqrt(4096)
+    assert not np.array_equal(R, S.rademacher(12346, 64, 4096))
+    st = S.Stream(12345)
+    u = np.array([st.next() for _ in range(20000)])
+    assert scs.kstest(u, "uniform").pvalue > 1e-3
+    c = np.corrcoef(u[:-1], u[1:])[0, 1]
+    assert abs(c) < 0.03
+    st = S.Stream(12345)
+    first = np.array([1.0 if st.next() < 0.5 else -1.0 for _ in range(4096)])
+    assert np.array_equal(first, R[0])
+    # the same checks on the raw Weyl sequence seed + k gamma (no mixing) fail
+    k = np.arange(1, 20001, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        weyl = ((np.uint64(12345) + k * np.uint64(S.GAMMA)) >> np.uint64(11)).astype(np.float64) / 2.0 ** 53
+    assert abs(np.corrcoef(weyl[:-1], weyl[1:])[0, 1]) > 0.03 or scs.kstest(weyl, "uniform").pvalue < 1e-3

@@ -187,13 +187,38 @@ def test_active_directions_closed_under_hierarchy():
         nd = ot.n_directions(h.w)
         assert np.isin(h.src * nd + h.dir_out, act[h.l][0]).all()
         assert np.isin(h.tgt * nd + h.dir_in, act[h.l][1]).all()
-    for l in act:
-        if l + 1 in act and act[l][0].size:
-            P, L = T.levels[l], T.levels[l + 1]
-            ndp, nd = ot.n_directions(P.w), ot.n_directions(L.w)
-            pb, pdir = np.divmod(act[l][0], ndp)
-            cd = ot.parent_direction(pdir, ot.n_cells(P.w))
-            for k in range(8):
-                ok = k < P.nchild[pb]
-                need = (P.child_first[pb[ok]] + k) * nd + cd[ok]
-                assert np.isin(need, act[l + 1][0]).all()
+    # both sides: outgoing (HF-M2M reads the children's direction containing
+    # the parent's) and incoming (HF-L2L writes it)
+    checked = 0
+    for side in (0, 1):
+        for l in act:
+            if l + 1 in act and act[l][side].size:
+                P, L = T.levels[l], T.levels[l + 1]
+                ndp, nd = ot.n_directions(P.w), ot.n_directions(L.w)
+                pb, pdir = np.divmod(act[l][side], ndp)
+                cd = ot.parent_direction(pdir, ot.n_cells(P.w))
+                for k in range(8):
+                    ok = k < P.nchild[pb]
+                    need = (P.child_first[pb[ok]] + k) * nd + cd[ok]
+                    assert np.isin(need, act[l + 1][side]).all()
+                    checked += need.size
+    assert checked > 0
+    # nothing beyond the closure: every active key is used by an M2L pair or
+    # needed by an active key of the parent level
+    for side in (0, 1):
+        for l in act:
+            L = T.levels[l]
+            nd = ot.n_directions(L.w)
+            used = set()
+            h = next((q for q in hf if q.l == l), None)
+            if h is not None:
+                used |= set((h.src * nd + h.dir_out if side == 0 else h.tgt * nd + h.dir_in).tolist())
+            if l - 1 in act:
+                P = T.levels[l - 1]
+                ndp = ot.n_directions(P.w)
+                pb, pdir = np.divmod(act[l - 1][side], ndp)
+                cd = ot.parent_direction(pdir, ot.n_cells(P.w))
+                for k in range(8):
+                    ok = k < P.nchild[pb]
+                    used |= set(((P.child_first[pb[ok]] + k) * nd + cd[ok]).tolist())
+            assert set(act[l][side].tolist()) == used
