@@ -194,6 +194,15 @@ def run_ours(args, wl):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     B.build()
+    probes = None
+    if rank == 0 and not args.no_probes:
+        # measured denominators (FP32 / FP64 FMA, MUFU, tcgen05 TF32 and F16), with the SM clock beside them
+        from paper_1311_4257_gb300.dfmm import measure_peaks
+        measure_peaks()   # warm-up: clocks ramp, modules load
+        pclk = Clocks(local)
+        pclk.start()
+        probes = measure_peaks()
+        probes["clocks"] = pclk.stop()
     K = wl["K"]
     p = points_of(wl)
     N = p.shape[0]
@@ -268,6 +277,16 @@ def run_ours(args, wl):
     prof = plan.profile_stop()
     torch.cuda.synchronize()
     pk = peaks()
+    if probes:
+        pk["fp32_tflops"] = probes["fp32_fma_tflops"]
+        pk["fp32_source"] = "measured (dfmm_measure_peaks, FP32 FMA probe)"
+    else:
+        pk["fp32_source"] = "derived: 152 SM x 128 lanes x 2 x max SM clock"
+    tc = (args.form == "tc") or (args.form == "auto" and wl["eps"] >= 1e-5)
+    # roofline of each stage family: translations on the tensor pipe (useful flops
+    # against the FP16 peak / 3 MMAs) or the FP32 pipe, P2P on the FP32 pipe,
+    # row streams and permutes on HBM
+    gemm_fams = ("m2l_hf", "m2l_lf", "m2m", "l2l", "p2l_proj")
     stages = {}
     for name, v in prof.items():
         per = v["ms"] / nprof
@@ -276,6 +295,16 @@ def run_ours(args, wl):
             entry["tflops"] = v["flops"] / (v["ms"] / 1e3) / 1e12
         if v["bytes"] > 0:
             entry["gbs"] = v["bytes"] / (v["ms"] / 1e3) / 1e9
+        if name in gemm_fams and "tflops" in entry:
+            pkv = pk["bf16_tflops"] / 3 if tc else pk["fp32_tflops"]
+            entry["frac"] = entry["tflops"] / pkv
+            entry["bound"] = "tensor (FP16 peak / 3)" if tc else "fp32 FMA"
+        elif name in ("p2p", "p2l_eval") and "tflops" in entry:
+            entry["frac"] = entry["tflops"] / pk["fp32_tflops"]
+            entry["bound"] = "fp32 FMA (16 + 8 nrhs flops per interaction)"
+        elif "gbs" in entry:
+            entry["frac"] = entry["gbs"] / pk["hbm_gbs"]
+            entry["bound"] = "hbm"
         stages[name] = entry
     # the dominant kernel: the translation-stage GEMM, over all its launches
     gfam = [k for k in ("m2l_hf", "m2l_lf", "m2m", "l2l", "p2l_proj") if k in prof]
@@ -284,7 +313,6 @@ def run_ours(args, wl):
     launches = sum(prof[k]["launches"] for k in gfam)
     achieved = g_flops / (g_ms / 1e3) / 1e12
     share = g_ms / sum(v["ms"] for v in prof.values())
-    tc = (args.form == "tc") or (args.form == "auto" and wl["eps"] >= 1e-5)
     if tc:
         # the scaled FP16 split issues 3 MMAs (hi hi, hi lo, lo hi) per useful
         # multiply-add; FP16 dense runs at the BF16 rate (measured)
@@ -297,8 +325,7 @@ def run_ours(args, wl):
     else:
         roofline = {"kernel": "gemm_stage_kernel (all translation stages)", "bound": "alu", "achieved": achieved,
                     "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["fp32_tflops"],
-                    "peak_source": "FP32 CUDA-core peak 152 SM x 128 lanes x 2 x %.0f MHz (%s clock)" % (
-                        pk["sm_max_mhz"], pk["source"])}
+                    "peak_source": "FP32 CUDA-core peak, %s" % pk["fp32_source"]}
     roofline.update({"traffic": traffic_for("gemm_tc_kernel", "m2l_tc.cu+dfmm.cpp", args.workload) if tc else
                      traffic_for("gemm_stage_kernel", "apply.cu+dfmm.cpp", args.workload),
                      "launches_per_step": launches / nprof, "ms_per_launch": g_ms / launches,
@@ -316,7 +343,7 @@ def run_ours(args, wl):
            "e2e": {"value": N * nrhs / (e2e_ms / 1e3), "unit": "points*RHS/s", "h2d_bytes_per_step": 8 * N * nrhs,
                    "d2h_bytes_per_step": 8 * N * nrhs},
            "gpu_launches": plan.launches(nrhs) * args.steps,
-           "clocks": clocks, "roofline": roofline, "stages": stages}
+           "clocks": clocks, "roofline": roofline, "stages": stages, "probes": probes}
     if args.compare and rank == 0:
         # the plain form (FP32 CUDA cores, one RHS) and the batched chosen form (16 RHS)
         plain = Plan(p, K, wl["eps"], cache_dir=args.cache_dir, m2l_mode=1)
@@ -600,7 +627,10 @@ def main():
     ap.add_argument("--cache-dir", default=os.path.join(tempfile.gettempdir(), "dfmm_cache"))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--form", default="auto", choices=["auto", "fp32", "tc"])
-    ap.add_argument("--compare", action="store_true", help="also time the plain FP32 form and 16 RHS")
+    ap.add_argument("--compare", dest="compare", action="store_true", default=True,
+                    help="also time the plain FP32 form and 16 RHS (default)")
+    ap.add_argument("--no-compare", dest="compare", action="store_false")
+    ap.add_argument("--no-probes", action="store_true", help="skip the peak-rate probes")
     ap.add_argument("--requests", type=int, default=2000, help="served8: requests in the stream")
     ap.add_argument("--rate", type=float, default=200.0, help="served8: Poisson arrival rate (1/s)")
     ap.add_argument("--budget-gb", type=float, default=64.0, help="served8: the server's device arena")

@@ -68,6 +68,22 @@ typedef struct {
                               the tensor cores, as a bit mask: 1 = HF M2L, 2 = LF M2L (V list),
                               4 = M2M, 8 = L2L, 16 = P2L projection; the others run on the FP32
                               CUDA cores.  For measuring the error each family's split adds. */
+  int32_t wait_test;       /* [0] testing aid for the failure path: with 1, the first CTA of every
+                              tensor-core translation launch waits on a barrier that nothing
+                              arrives at.  Its bounded wait gives up after 0.2 s, the launch (and
+                              the rest of the apply's tensor-core launches) stop early, and
+                              dfmm_sync_status returns DFMM_ERR_TIMEOUT.  The potentials of such
+                              an apply are undefined. */
+  int32_t tile_order;      /* [0] order of a translation stage's work tiles: 0 = by block of
+                              target rows when the stage's operators total at most 64 MB (they
+                              stay in L2), else by operator (each read from DRAM once); 1 = always
+                              by target block; 2 = always by operator.  The result is the same up
+                              to the order of the floating-point additions. */
+  int32_t p2p_mode;        /* [0] near-field form: 0 = automatic (1);
+                              1 = double-float box-local coordinates; 2 = FP32 coordinates, with
+                              the pairs closer than min(0.5, 1e-6 / eps) wavelengths corrected
+                              exactly (listed at plan time).  Form 2 falls back to 1 when two
+                              distinct points round to the same FP32 coordinates. */
 } dfmm_options;
 
 /* Build a plan (Sec. 2.2 octree, lists, Eq. 2 representations and the
@@ -101,8 +117,9 @@ int dfmm_apply_host(dfmm_plan_t plan, const void* f_host, void* u_host, int nrhs
                     cudaStream_t stream);
 
 /* Read back the device status word of the last apply on `stream`
- * (synchronises the stream).  Returns DFMM_OK, DFMM_ERR_TIMEOUT or
- * DFMM_ERR_DEVICE. */
+ * (synchronises the stream), together with that of the last
+ * dfmm_apply_noalloc on the current device if that call was issued on
+ * `stream`.  Returns DFMM_OK, DFMM_ERR_TIMEOUT or DFMM_ERR_DEVICE. */
 int dfmm_sync_status(dfmm_plan_t plan, cudaStream_t stream);
 
 /* Free every resource of the plan (waits for the device first). */
@@ -129,6 +146,7 @@ typedef struct {
   double m2l_flops;            /* algorithmic M2L flops per RHS: 8 r_t r_s per pair */
   double other_translation_flops; /* M2M, L2L, LF-M2L, P2M/L2P GEMMs per RHS */
   int64_t hf_ops[32];          /* distinct HF-M2L operators per level (offsets up to cube symmetry) */
+  int64_t p2p_close_pairs;     /* FP32 near field: pairs with a stored exact correction */
 } dfmm_stats;
 
 int dfmm_plan_stats(dfmm_plan_t plan, dfmm_stats* out);
@@ -177,24 +195,27 @@ int dfmm_export(dfmm_plan_t plan, int what, void* buffer, int64_t* count);
 /* The matvec of dfmm_apply without allocating device memory.
  *
  * The paper has no counterpart: this entry point serves callers that must not
- * let a library call cudaMalloc or cudaFree, such as code running while a
- * CUDA graph is captured, request paths of services that forbid allocation
- * after start-up, or hosts whose device memory is budgeted in advance.
- * Every per-apply buffer (sorted densities and potentials, the translation
- * states, the staging buffers and the work tables) is laid out in one
- * file-scope device array of dfmm_noalloc_capacity() bytes (64 MiB), which
- * every device that loads the library holds until the process exits.
+ * let a library call cudaMalloc or cudaFree, such as request paths of services
+ * that forbid allocation after start-up (the allocator belongs to someone
+ * else, or its latency and failures are not allowed there) and hosts whose
+ * device memory is budgeted in advance.  Every per-apply buffer (the status
+ * word, sorted densities and potentials, the translation states, the staging
+ * buffers and the work tables) is laid out in one file-scope device array of
+ * dfmm_noalloc_capacity() bytes (64 MiB), which every device that loads the
+ * library holds until the process exits.
  *   plan, f, u, nrhs, stream : as for dfmm_apply (device pointers, complex64
  *            [nrhs][N], u overwritten).  The plan must belong to the current
  *            device.
- * Returns DFMM_ERR_UNSUPPORTED, with the required size in the message, when
- * the apply needs more scratch than the array holds (roughly N * nrhs above
- * 10^5 at the default tolerances).
+ * An apply fits exactly when dfmm_apply_workspace_bytes(plan, nrhs) <=
+ * dfmm_noalloc_capacity(); otherwise the call returns DFMM_ERR_UNSUPPORTED,
+ * with the required size in the message, and enqueues nothing.
  * The first call on a device looks up the array's device address on that
- * device; make that first call before any stream capture.  All calls share
+ * device (make that first call before any stream capture).  All calls share
  * the one array and each overwrites what the previous left there: calls that
  * overlap on the GPU (other streams, other threads) race on it and must be
- * serialised by the caller. */
+ * serialised by the caller.  The status word of the last such apply on the
+ * current device is read back by dfmm_sync_status (with any plan and the
+ * stream of that apply). */
 int dfmm_apply_noalloc(dfmm_plan_t plan, const void* f, void* u, int nrhs, cudaStream_t stream);
 
 /* Size in bytes of the scratch array of dfmm_apply_noalloc. */
@@ -321,6 +342,28 @@ int64_t dfmm_apply_launches(dfmm_plan_t plan, int nrhs);
  *   cap     : capacity of b2/a2 in points; DFMM_ERR_INVALID if 2r > cap. */
 int dfmm_representation(double w, int cell, double w_top, double eps_op, int sample_box, int sample_far,
                         int sketch_rows, int* r_out, double* b2, double* a2, int cap);
+
+/* Measured peak rates of the current GPU, for roofline denominators (the
+ * paper has no counterpart).  Each rate comes from a short probe kernel of
+ * independent chains on all SMs, timed with CUDA events after one warm-up
+ * launch: fused multiply-adds on the CUDA cores (FP32 and FP64, 2 flops
+ * each), fast sine + cosine pairs and reciprocal square roots on the
+ * special-function unit, and dense tcgen05 MMAs (M = 128, N = 256, one CTA
+ * per SM, operands from shared memory) of kind::tf32 and kind::f16.  The
+ * rates depend on the SM clock at the time; sample it beside the call.
+ * Allocates 4 KB of device memory; synchronises the device. */
+typedef struct {
+  int32_t sm_count;
+  int32_t reserved;
+  double fp32_fma_tflops;
+  double fp64_fma_tflops;
+  double sincos_gops;        /* sine + cosine pairs per second, 1e9 */
+  double rsqrt_gops;
+  double tf32_mma_tflops;
+  double f16_mma_tflops;
+} dfmm_peaks;
+
+int dfmm_measure_peaks(dfmm_peaks* out);
 
 /* Thread-local message of the last failed call on this thread. */
 const char* dfmm_last_error(void);

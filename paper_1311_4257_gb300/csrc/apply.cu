@@ -516,6 +516,221 @@ __global__ __launch_bounds__(P2P_THREADS) void p2p_kernel(P2PArgs a) {
   }
 }
 
+// ------------------------------------------------------------------------
+// FP32 form of the near field.  Coordinates are the high parts alone: a
+// source point is shifted into the target leaf's frame once, when it is staged,
+// and every pair then costs three subtractions for its difference.  Their
+// rounding (about 1e-7 absolute) matters only for close pairs, whose 1/d
+// amplitude it perturbs by 1e-7 / d relative: the plan lists every pair closer
+// than delta and stores its exact correction G(p_i, p_j) - g32 (FP64 at plan
+// time), added at the end.  Only points of the target leaf itself can
+// coincide (equal points have equal Morton keys), so only that entry of the U
+// list, kept first, takes the guarded form.
+
+constexpr int PF_THREADS = 128;
+constexpr int PF_CHUNK = 512;
+constexpr int PF_LEAVES = 64;
+
+// The FP32 form's kernel value for one pair: target x and source y in the target
+// leaf's frame.  Every rounding is explicit, so the close-pair pass reproduces
+// the main loop's value exactly.  guarded: a coincident pair gives 0.
+template <bool guarded>
+__device__ __forceinline__ float2 g32(float xx, float xy, float xz, float4 y) {
+  const float dx = __fsub_rn(xx, y.x), dy = __fsub_rn(xy, y.y), dz = __fsub_rn(xz, y.z);
+  const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+  const float inv = guarded ? (r2 > 0.f ? rsqrtf(r2) : 0.f) : rsqrtf(r2);
+  const float d = __fmul_rn(r2, inv);
+  const float ph = __fsub_rn(d, rintf(d));
+  float sn, cs;
+  __sincosf(__fmul_rn(6.28318530717958647f, ph), &sn, &cs);
+  return make_float2(__fmul_rn(cs, inv), __fmul_rn(sn, inv));
+}
+
+__device__ __forceinline__ float4 shifted(float4 v, float4 sh) {
+  return make_float4(__fadd_rn(v.x, sh.x), __fadd_rn(v.y, sh.y), __fadd_rn(v.z, sh.z), 0.f);
+}
+
+// One block per target leaf; each thread holds two targets (t and t + nth), so
+// a staged source is read from shared memory once per two interactions; the
+// threads form groups that split the staged sources.  NR right-hand sides per
+// pass.
+template <int NR>
+__global__ __launch_bounds__(PF_THREADS) void p2p_fast_kernel(P2PArgs a) {
+  __shared__ float4 sy[PF_CHUNK];
+  __shared__ float2 sf[PF_CHUNK][NR];
+  __shared__ float2 red[PF_THREADS][2][NR];
+  __shared__ int4 su[PF_LEAVES];
+  __shared__ float4 ssh[PF_LEAVES];
+  __shared__ int soff[PF_LEAVES + 1];
+  const int2 lr = a.leaf_range[blockIdx.x];
+  const int64_t u0 = a.u_off[blockIdx.x], u1 = a.u_off[blockIdx.x + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t0 = 0; t0 < lr.y; t0 += 2 * PF_THREADS) {
+    const int nt = min(2 * PF_THREADS, lr.y - t0);
+    const int nth = (nt + 1) >> 1;
+    const int ngrp = PF_THREADS / nth;
+    const int ti = threadIdx.x % nth, grp = threadIdx.x / nth;
+    const bool active = grp < ngrp;
+    const int i1 = ti + nth < nt ? ti + nth : ti;   // an odd count repeats the last target
+    const float4 x0 = a.pts[lr.x + t0 + ti];
+    const float4 x1 = a.pts[lr.x + t0 + i1];
+    for (int r0 = 0; r0 < a.nrhs; r0 += NR) {
+      const int nr = min(NR, a.nrhs - r0);
+      float2 acc0[NR], acc1[NR];
+#pragma unroll
+      for (int k = 0; k < NR; ++k) acc0[k] = acc1[k] = make_float2(0.f, 0.f);
+      for (int64_t ub = u0; ub < u1; ub += PF_LEAVES) {
+        const int nb = (int)(u1 - ub < PF_LEAVES ? u1 - ub : PF_LEAVES);
+        __syncthreads();   // the previous batch has been consumed
+        if (threadIdx.x < nb) {
+          const int4 e = a.u_src[ub + threadIdx.x];
+          su[threadIdx.x] = e;
+          ssh[threadIdx.x] = a.shifts[e.z];
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {   // exclusive prefix of the leaf sizes
+          int v0 = lane < nb ? su[lane].y : 0;
+          int v1 = lane + 32 < nb ? su[lane + 32].y : 0;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, v0, o);
+            int w = __shfl_up_sync(0xffffffffu, v1, o);
+            if (lane >= o) { v0 += t; v1 += w; }
+          }
+          v1 += __shfl_sync(0xffffffffu, v0, 31);
+          soff[lane + 1] = v0;
+          soff[lane + 33] = v1;
+          if (lane == 0) soff[0] = 0;
+        }
+        __syncthreads();
+        const int total = soff[nb];
+        const int self_end = (ub == u0 && su[0].w) ? soff[1] : 0;   // staged indices of the own leaf
+        for (int c0 = 0; c0 < total; c0 += PF_CHUNK) {
+          const int fill = min(PF_CHUNK, total - c0);
+          if (c0 > 0) __syncthreads();
+          // one warp per U entry: its points, shifted into this leaf's frame
+          for (int e = warp; e < nb; e += PF_THREADS / 32) {
+            const int lo = max(soff[e], c0), hi = min(soff[e + 1], c0 + fill);
+            const int base = su[e].x - soff[e];
+            const float4 sh = ssh[e];
+            for (int q = lo + lane; q < hi; q += 32) {
+              const int j = base + q;
+              sy[q - c0] = shifted(a.pts[j], sh);
+#pragma unroll
+              for (int k = 0; k < NR; ++k)
+                sf[q - c0][k] = k < nr ? a.fs[(int64_t)j * a.nrhs + r0 + k] : make_float2(0.f, 0.f);
+            }
+          }
+          __syncthreads();
+          if (active) {
+            const int self_hi = min(max(self_end - c0, 0), fill);
+            int j = grp;
+            for (; j < self_hi; j += ngrp) {
+              const float4 y = sy[j];
+              const float2 g0 = g32<true>(x0.x, x0.y, x0.z, y), g1 = g32<true>(x1.x, x1.y, x1.z, y);
+#pragma unroll
+              for (int k = 0; k < NR; ++k) {
+                const float2 f = sf[j][k];
+                acc0[k].x = fmaf(g0.x, f.x, fmaf(-g0.y, f.y, acc0[k].x));
+                acc0[k].y = fmaf(g0.x, f.y, fmaf(g0.y, f.x, acc0[k].y));
+                acc1[k].x = fmaf(g1.x, f.x, fmaf(-g1.y, f.y, acc1[k].x));
+                acc1[k].y = fmaf(g1.x, f.y, fmaf(g1.y, f.x, acc1[k].y));
+              }
+            }
+#pragma unroll 4
+            for (; j < fill; j += ngrp) {
+              const float4 y = sy[j];
+              const float2 g0 = g32<false>(x0.x, x0.y, x0.z, y), g1 = g32<false>(x1.x, x1.y, x1.z, y);
+#pragma unroll
+              for (int k = 0; k < NR; ++k) {
+                const float2 f = sf[j][k];
+                acc0[k].x = fmaf(g0.x, f.x, fmaf(-g0.y, f.y, acc0[k].x));
+                acc0[k].y = fmaf(g0.x, f.y, fmaf(g0.y, f.x, acc0[k].y));
+                acc1[k].x = fmaf(g1.x, f.x, fmaf(-g1.y, f.y, acc1[k].x));
+                acc1[k].y = fmaf(g1.x, f.y, fmaf(g1.y, f.x, acc1[k].y));
+              }
+            }
+          }
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int k = 0; k < NR; ++k) {
+        red[threadIdx.x][0][k] = active ? acc0[k] : make_float2(0.f, 0.f);
+        red[threadIdx.x][1][k] = active ? acc1[k] : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      for (int tt = threadIdx.x; tt < nt; tt += PF_THREADS) {
+        const int th = tt < nth ? tt : tt - nth, slot = tt < nth ? 0 : 1;
+        const int64_t i = lr.x + t0 + tt;
+        const int c0 = a.close_off[i], c1 = a.close_off[i + 1];
+        for (int k = 0; k < nr; ++k) {
+          float2 sum = make_float2(0.f, 0.f);
+          for (int g = 0; g < ngrp; ++g) {
+            const float2 v = red[g * nth + th][slot][k];
+            sum.x += v.x;
+            sum.y += v.y;
+          }
+          for (int c = c0; c < c1; ++c) {   // exact corrections of the close pairs
+            const float2 w = a.close_w[c];
+            const float2 f = a.fs[(int64_t)a.close_j[c] * a.nrhs + r0 + k];
+            sum.x = fmaf(w.x, f.x, fmaf(-w.y, f.y, sum.x));
+            sum.y = fmaf(w.x, f.y, fmaf(w.y, f.x, sum.y));
+          }
+          float2* uu = a.us + i * a.nrhs + r0 + k;
+          const float2 o = *uu;
+          *uu = make_float2(o.x + sum.x, o.y + sum.y);
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Close pairs of the FP32 form (plan time): one thread per target point walks
+// its leaf's U list.  Pass 1 counts, pass 2 writes (j, G - g32) with G in FP64
+// from the double-float coordinates.
+__global__ void p2p_close_kernel(P2PArgs a, float delta2, int32_t* cnt, unsigned* degenerate,
+                                 const int32_t* off, int32_t* cj, float2* cw) {
+  const int64_t leaf = blockIdx.x;
+  const int2 lr = a.leaf_range[leaf];
+  const int64_t u0 = a.u_off[leaf], u1 = a.u_off[leaf + 1];
+  for (int t = threadIdx.x; t < lr.y; t += blockDim.x) {
+    const int64_t i = lr.x + t;
+    const float4 x = a.pts[i], xl = a.pts_lo[i];
+    int n = 0;
+    for (int64_t e = u0; e < u1; ++e) {
+      const int4 ue = a.u_src[e];
+      const float4 sh = a.shifts[ue.z];
+      for (int q = 0; q < ue.y; ++q) {
+        const int j = ue.x + q;
+        const float4 v = a.pts[j], vl = a.pts_lo[j];
+        const float4 y = shifted(v, sh);
+        const float dx = __fsub_rn(x.x, y.x), dy = __fsub_rn(x.y, y.y), dz = __fsub_rn(x.z, y.z);
+        const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
+        const bool same = ue.w && v.x == x.x && v.y == x.y && v.z == x.z && vl.x == xl.x && vl.y == xl.y &&
+                          vl.z == xl.z;
+        if (same || !(r2 < delta2)) continue;
+        if (r2 == 0.f) atomicOr(degenerate, 1u);
+        if (off) {
+          const double ex = ((double)x.x + (double)xl.x) - ((double)v.x + (double)vl.x + (double)sh.x);
+          const double ey = ((double)x.y + (double)xl.y) - ((double)v.y + (double)vl.y + (double)sh.y);
+          const double ez = ((double)x.z + (double)xl.z) - ((double)v.z + (double)vl.z + (double)sh.z);
+          const double d = sqrt(ex * ex + ey * ey + ez * ez);
+          double sn, cs;
+          sincospi(2.0 * d, &sn, &cs);
+          const float2 g = g32<true>(x.x, x.y, x.z, y);
+          const int64_t c = off[i] + n;
+          cj[c] = j;
+          cw[c] = make_float2((float)(cs / d - (double)g.x), (float)(sn / d - (double)g.y));
+        }
+        ++n;
+      }
+    }
+    if (!off) cnt[i] = n;
+  }
+}
+
 }  // namespace
 
 void launch_gemm_stage(const GemmArgs& a, cudaStream_t s) {
@@ -571,6 +786,21 @@ void launch_p2m_rows(const P2MRowsArgs& a, cudaStream_t s) {
   const unsigned grid = (unsigned)((a.njobs + 7) / 8);
   if (a.R <= 128) p2m_rows_kernel<2><<<grid, 256, 0, s>>>(a);
   else p2m_rows_kernel<4><<<grid, 256, 0, s>>>(a);
+  DFMM_CUDA(cudaGetLastError());
+}
+
+void launch_p2p_fast(const P2PArgs& a, cudaStream_t s) {
+  if (a.nleaves == 0) return;
+  if (a.nrhs == 1) p2p_fast_kernel<1><<<(unsigned)a.nleaves, PF_THREADS, 0, s>>>(a);
+  else if (a.nrhs == 2) p2p_fast_kernel<2><<<(unsigned)a.nleaves, PF_THREADS, 0, s>>>(a);
+  else p2p_fast_kernel<4><<<(unsigned)a.nleaves, PF_THREADS, 0, s>>>(a);
+  DFMM_CUDA(cudaGetLastError());
+}
+
+void launch_p2p_close(const P2PArgs& a, float delta, int32_t* cnt, unsigned* degenerate, const int32_t* off,
+                      int32_t* close_j, float2* close_w, cudaStream_t s) {
+  if (a.nleaves == 0) return;
+  p2p_close_kernel<<<(unsigned)a.nleaves, 64, 0, s>>>(a, delta * delta, cnt, degenerate, off, close_j, close_w);
   DFMM_CUDA(cudaGetLastError());
 }
 

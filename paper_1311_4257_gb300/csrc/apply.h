@@ -29,6 +29,8 @@ struct GemmArgs {
   int nrhs;
   int store;                // 1: every target row of the stage has one pair and nothing wrote it
                             //    earlier in the apply, so results are stored, not added
+  int wait_test;            // tensor-core form: 1 = CTA 0 waits on a barrier nothing arrives at
+                            //    (exercises the bounded-wait failure path)
 };
 
 void launch_gemm_stage(const GemmArgs& a, cudaStream_t s);
@@ -116,14 +118,28 @@ struct P2PArgs {
   const int2* leaf_range;    // (first, count) per target leaf
   int64_t nleaves;
   const int64_t* u_off;      // CSR offsets per target leaf
-  const int4* u_src;         // (first, count, shift index, 0) per source leaf
+  const int4* u_src;         // (first, count, shift index, self) per source leaf; the target
+                             //   leaf's own entry comes first, with self = 1
   const float4* shifts;      // c_src - c_tgt
   const float4* pts;         // local (x, y, z, |x|^2), high parts
   const float4* pts_lo;      // low parts of the local coordinates
   const float2* fs;
   float2* us;
   int nrhs;
+  // FP32 form only: close-pair corrections, CSR per sorted target point
+  const int32_t* close_off;  // [N + 1]
+  const int32_t* close_j;    // source point of each correction
+  const float2* close_w;     // G(p_i, p_j) - (the FP32 form's value for the pair)
 };
+// Double-float coordinates throughout (any accuracy).
 void launch_p2p(const P2PArgs& a, cudaStream_t s);
+// FP32 coordinates (high parts) throughout, plus the close-pair corrections.
+void launch_p2p_fast(const P2PArgs& a, cudaStream_t s);
+// Close pairs of the FP32 form: every (target i, source j) of the U lists with
+// FP32 distance below delta and p_j != p_i.  Pass 1 (off == nullptr): counts per
+// target point into cnt[N], and sets *degenerate if two distinct points have FP32
+// distance 0.  Pass 2: fills j and w at the CSR offsets off[N + 1].
+void launch_p2p_close(const P2PArgs& a, float delta, int32_t* cnt, unsigned* degenerate, const int32_t* off,
+                      int32_t* close_j, float2* close_w, cudaStream_t s);
 
 }  // namespace dfmm

@@ -191,6 +191,12 @@ struct dfmm_plan_s {
   int64_t* p2p_off = nullptr;
   int4* p2p_src = nullptr;
   float4* p2p_shift = nullptr;
+  int32_t* close_off = nullptr;   // FP32 near field: close-pair corrections (CSR per sorted point)
+  int32_t* close_j = nullptr;
+  float2* close_w = nullptr;
+  int64_t n_close = 0;
+  double close_delta = 0;
+  std::unique_ptr<DevArena> close_keep;   // their storage (allocated after a scratch mark of the plan arena)
   int64_t n_leaves = 0;
   float4* zero_shift = nullptr;
   std::unique_ptr<RepSet> reps;
@@ -971,7 +977,10 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
         shift_id[key] = sid;
         shifts.push_back(make_float4((float)sh[0], (float)sh[1], (float)sh[2], 0.f));
       } else sid = it->second;
-      per[gleaf.at({lb, b})].push_back(make_int4(LV[la].h_first[a], LV[la].h_count[a], sid, 0));
+      const int self = (la == lb && a == b) ? 1 : 0;   // the leaf's own entry: may hold coincident points
+      auto& lst = per[gleaf.at({lb, b})];
+      lst.push_back(make_int4(LV[la].h_first[a], LV[la].h_count[a], sid, self));
+      if (self) std::swap(lst.front(), lst.back());   // kept first
       inter += (int64_t)LV[lb].h_count[b] * LV[la].h_count[a];
     }
     std::vector<int64_t> off(leaf_range.size() + 1, 0);
@@ -985,10 +994,50 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
     P->p2p_src = upload(src, ar, s);
     P->p2p_shift = upload(shifts, ar, s);
     P->stats.p2p_interactions = inter;
+    // FP32 form of the near field: its close pairs and their exact corrections
+    // (the pairs closer than delta = 1e-6 / eps, at most 0.5; the FP32
+    // coordinates' rounding perturbs a pair at distance d by about 1e-7 / d)
+    if (P->opt.p2p_mode == 2 && P->n_leaves > 0) {
+      P2PArgs pa{};
+      pa.leaf_range = P->p2p_range;
+      pa.nleaves = P->n_leaves;
+      pa.u_off = P->p2p_off;
+      pa.u_src = P->p2p_src;
+      pa.shifts = P->p2p_shift;
+      pa.pts = P->pts_local;
+      pa.pts_lo = P->pts_lo;
+      const float delta = (float)std::min(0.5, 1e-6 / P->eps);
+      ArenaMark mk(ar);
+      int32_t* cnt = ar.alloc<int32_t>(N);
+      unsigned* degen = ar.alloc<unsigned>(1);
+      DFMM_CUDA(cudaMemsetAsync(degen, 0, 4, s));
+      launch_p2p_close(pa, delta, cnt, degen, nullptr, nullptr, nullptr, s);
+      std::vector<int32_t> hc(N);
+      unsigned hd = 0;
+      DFMM_CUDA(cudaMemcpyAsync(hc.data(), cnt, N * 4, cudaMemcpyDeviceToHost, s));
+      DFMM_CUDA(cudaMemcpyAsync(&hd, degen, 4, cudaMemcpyDeviceToHost, s));
+      DFMM_CUDA(cudaStreamSynchronize(s));
+      P->close_delta = delta;
+      if (hd) {
+        P->opt.p2p_mode = 1;   // two distinct points share FP32 coordinates: double-float form
+      } else {
+        std::vector<int32_t> ho(N + 1, 0);
+        for (int64_t i = 0; i < N; ++i) ho[i + 1] = ho[i] + hc[i];
+        P->n_close = ho[N];
+        P->close_keep.reset(new DevArena());
+        DevArena& ca = *P->close_keep;
+        P->close_off = upload(ho, ca, s);
+        P->close_j = ca.alloc<int32_t>(std::max<int64_t>(1, P->n_close));
+        P->close_w = ca.alloc<float2>(std::max<int64_t>(1, P->n_close));
+        launch_p2p_close(pa, delta, nullptr, degen, P->close_off, P->close_j, P->close_w, s);
+        DFMM_CUDA(cudaStreamSynchronize(s));
+      }
+    }
   }
   P->stats.m2l_flops = m2l_flops;
   P->stats.other_translation_flops = other_flops;
-  P->stats.plan_bytes = (int64_t)ar.bytes();
+  P->stats.plan_bytes = (int64_t)ar.bytes() + (P->close_keep ? (int64_t)P->close_keep->bytes() : 0);
+  P->stats.p2p_close_pairs = P->n_close;
   P->stats.plan_seconds = now() - t0;
 }
 
@@ -1083,12 +1132,13 @@ bool on_tensor_cores(const dfmm_plan_s* P, const GemmPlan& g) {
   return P->opt.m2l_mode == 2 && gemm_tc_supported(g.M, g.Kd) && (P->opt.tc_stages & kTcFamBit[g.fam]) != 0;
 }
 
-std::vector<int4> make_tiles(const GemmPlan& g, int nrhs, int cols) {
+// tile_order: 0 = by the 64 MB rule above, 1 = always by target block, 2 = always by operator.
+std::vector<int4> make_tiles(const GemmPlan& g, int nrhs, int cols, int tile_order) {
   const int per = std::max(1, cols / nrhs);
   std::vector<int4> t;
   std::vector<int64_t> key;
   const int64_t row_bytes = (int64_t)g.M * 8 * nrhs;
-  const bool blocked = (double)g.nops * g.M * g.Kd * 8.0 <= 64.0 * (1 << 20);
+  const bool blocked = tile_order == 1 || (tile_order == 0 && (double)g.nops * g.M * g.Kd * 8.0 <= 64.0 * (1 << 20));
   const int64_t block_rows = blocked ? std::max<int64_t>(1, ((int64_t)8 << 20) / std::max<int64_t>(1, row_bytes))
                                      : ((int64_t)1 << 40);
   for (const int4& grp : g.groups)
@@ -1105,12 +1155,13 @@ std::vector<int4> make_tiles(const GemmPlan& g, int nrhs, int cols) {
   return out;
 }
 
-std::pair<int4*, int64_t> tiles_for(Workspace* W, const GemmPlan& g, int nrhs, int cols, cudaStream_t s) {
+std::pair<int4*, int64_t> tiles_for(const dfmm_plan_s* P, Workspace* W, const GemmPlan& g, int nrhs, int cols,
+                                    cudaStream_t s) {
   auto key = std::make_pair((const void*)&g, nrhs * 1024 + cols);
   auto it = W->tiles.find(key);
   if (it != W->tiles.end()) return it->second;
   if (W->external) throw Error(DFMM_ERR_INVALID, "work tiles missing from the carved workspace");
-  std::vector<int4> t = make_tiles(g, nrhs, cols);
+  std::vector<int4> t = make_tiles(g, nrhs, cols, P->opt.tile_order);
   int4* d = W->ar.alloc<int4>(std::max<size_t>(1, t.size()));
   if (!t.empty()) DFMM_CUDA(cudaMemcpyAsync(d, t.data(), t.size() * sizeof(int4), cudaMemcpyHostToDevice, s));
   W->tiles[key] = {d, (int64_t)t.size()};
@@ -1144,7 +1195,7 @@ struct Runner {
     const bool split = tc && (src_key < 0 || src_key != split_key);
     if (tc) split_key = src_key;
     if (count) { count[0] += split ? 2 : 1; return; }
-    auto t = tiles_for(W, g, nrhs, tc ? gemm_tc_columns() : 64, s);
+    auto t = tiles_for(P, W, g, nrhs, tc ? gemm_tc_columns() : 64, s);
     GemmArgs a;
     a.ops = g.ops;
     a.M = g.M;
@@ -1158,6 +1209,7 @@ struct Runner {
     a.dst_ld = dst_ld;
     a.nrhs = nrhs;
     a.store = (first && g.dst_unique) ? 1 : 0;
+    a.wait_test = P->opt.wait_test ? 1 : 0;
     if (tc) {
       if (split) {
         ProfScope ps(W, s, F_SPLIT, 0.0, (double)src_rows * nrhs * src_ld * 16);
@@ -1313,7 +1365,11 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
     a.fs = W->fs;
     a.us = W->us;
     a.nrhs = nrhs;
-    launch_p2p(a, s);
+    a.close_off = P->close_off;
+    a.close_j = P->close_j;
+    a.close_w = P->close_w;
+    if (P->opt.p2p_mode == 2) launch_p2p_fast(a, s);
+    else launch_p2p(a, s);
   });
   R.launch(F_PERMUTE, 0.0, 20.0 * N * nrhs, [&] { launch_permute_out(W->us, P->perm, N, nrhs, u, s); });
 }
@@ -1327,8 +1383,8 @@ std::vector<const GemmPlan*> all_gemms(dfmm_plan_s* P) {
 }
 
 // Lays out the whole workspace of an apply with nrhs right-hand sides inside
-// [base, base + bytes): state buffers, staging buffers and the work tiles of
-// every stage (copied in on `s`).  No device memory is allocated.  With
+// [base, base + bytes): the device status word (at offset 0), state buffers,
+// staging buffers and the work tiles of every stage (copied in on `s`).  No device memory is allocated.  With
 // base == nullptr nothing is laid out or copied: the return value is the
 // number of bytes the layout needs.
 size_t carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaStream_t s, Workspace& W) {
@@ -1342,6 +1398,9 @@ size_t carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaS
   const int64_t N = P->N;
   W.external = true;
   W.nrhs = nrhs;
+  // the device status word first, at offset 0 of the region (reset by every apply)
+  W.status = (unsigned*)take(4);
+  W.zero.push_back({W.status, 4});
   W.fs = (float2*)take((size_t)N * nrhs * 8);
   W.us = (float2*)take((size_t)N * nrhs * 8);
   W.zero.push_back({W.us, (size_t)N * nrhs * 8});
@@ -1370,15 +1429,13 @@ size_t carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaS
     W.alo = (__half*)take(e * 2);
     W.ascale = (float*)take((size_t)max_source_rows(P) * nrhs * 4);
   }
-  W.status = (unsigned*)take(4);
-  W.zero.push_back({W.status, 4});
   std::vector<std::pair<const GemmPlan*, std::vector<int4>>> tl;
   std::vector<int> tl_cols;
   for (const GemmPlan* g : all_gemms(P)) {
     if (g->npairs == 0) continue;
     const int cols = on_tensor_cores(P, *g) ? gemm_tc_columns() : 64;
     tl_cols.push_back(cols);
-    tl.push_back({g, make_tiles(*g, nrhs, cols)});
+    tl.push_back({g, make_tiles(*g, nrhs, cols, P->opt.tile_order)});
   }
   std::vector<int4*> dst(tl.size());
   for (size_t k = 0; k < tl.size(); ++k) dst[k] = (int4*)take(tl[k].second.size() * sizeof(int4));
@@ -1410,7 +1467,7 @@ void build_images(dfmm_plan_s* P, cudaStream_t s) {
     build_tc_image(g->ops, g->M, g->Kd, g->nops, g->img, g->op_scale, s);
   }
   DFMM_CUDA(cudaStreamSynchronize(s));
-  P->stats.plan_bytes = (int64_t)P->ar.bytes();
+  P->stats.plan_bytes = (int64_t)P->ar.bytes() + (P->close_keep ? (int64_t)P->close_keep->bytes() : 0);
 }
 
 template <class F>
@@ -1508,6 +1565,12 @@ int dfmm_plan(const double* points, int64_t N, double K, double eps, const dfmm_
     if (o.m2l_mode == 0) o.m2l_mode = eps >= 1e-5 ? 2 : 1;
     if (o.tc_stages < 0 || o.tc_stages > 31) return fail(DFMM_ERR_INVALID, "tc_stages must be a mask in [0, 31]");
     if (o.tc_stages == 0) o.tc_stages = 31;
+    if (o.wait_test < 0 || o.wait_test > 1) return fail(DFMM_ERR_INVALID, "wait_test must be 0 or 1");
+    if (o.tile_order < 0 || o.tile_order > 2) return fail(DFMM_ERR_INVALID, "tile_order must be 0, 1 or 2");
+    if (o.p2p_mode < 0 || o.p2p_mode > 2) return fail(DFMM_ERR_INVALID, "p2p_mode must be 0, 1 or 2");
+    // automatic near field: double-float coordinates (the FP32 form with
+    // close-pair corrections is selected explicitly)
+    if (o.p2p_mode == 0) o.p2p_mode = 1;
     std::unique_ptr<dfmm_plan_s> P(new dfmm_plan_s());
     DFMM_CUDA(cudaGetDevice(&P->device));
     P->N = N;
@@ -1566,9 +1629,13 @@ int dfmm_sync_status(dfmm_plan_t plan, cudaStream_t stream) {
     DFMM_CUDA(cudaStreamSynchronize(stream));
     std::lock_guard<std::mutex> g(plan->ws_mu);
     auto it = plan->ws.find(stream);
-    if (it == plan->ws.end()) return DFMM_OK;
     unsigned st = 0;
-    DFMM_CUDA(cudaMemcpy(&st, it->second->status, 4, cudaMemcpyDeviceToHost));
+    if (it != plan->ws.end()) DFMM_CUDA(cudaMemcpy(&st, it->second->status, 4, cudaMemcpyDeviceToHost));
+    if (const unsigned* na = noalloc_status_word(stream)) {   // the last allocation-free apply, if on this stream
+      unsigned sn = 0;
+      DFMM_CUDA(cudaMemcpy(&sn, na, 4, cudaMemcpyDeviceToHost));
+      st |= sn;
+    }
     if (st & kStatusTimeout) return fail(DFMM_ERR_TIMEOUT, "a device wait gave up");
     if (st) return fail(DFMM_ERR_DEVICE, "a device-side check failed");
     return DFMM_OK;

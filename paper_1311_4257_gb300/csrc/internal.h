@@ -16,4 +16,9 @@ int set_error(int code, const char* msg);
 int apply_with_scratch(dfmm_plan_s* plan, const void* f, void* u, int nrhs, cudaStream_t stream, void* scratch,
                        size_t bytes);
 
+// Device address of the status word of the last allocation-free apply on the
+// current device (offset 0 of its scratch array) if that apply was issued on
+// `stream`, else nullptr.
+const unsigned* noalloc_status_word(cudaStream_t stream);
+
 }  // namespace dfmm

@@ -58,7 +58,7 @@ constexpr int TC_STAGES = 4;
 constexpr int A_BYTES = TC_M * TC_BK * 2;          // 8 KB
 constexpr int B_BYTES = TC_NMAX * TC_BK * 2;       // 16 KB
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-constexpr int SMEM_BYTES = TC_STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int SMEM_BYTES = TC_STAGES * STAGE_BYTES + 1024 + 256;   // stages, alignment, barriers
 constexpr int TMEM_COLS = 512;                     // two accumulators of up to 256 columns
 constexpr int CORE_SBO = (TC_BK / 8) * 128;        // 512 B between 8-row groups
 constexpr unsigned long long WAIT_NS = 200000000ull;    // 0.2 s bound on every wait
@@ -295,7 +295,8 @@ __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcAr
   uint64_t* empty = full + TC_STAGES;
   uint64_t* acc_full = empty + TC_STAGES;
   uint64_t* acc_empty = acc_full + 1;
-  uint32_t* tmem_slot = (uint32_t*)(acc_empty + 1);
+  uint64_t* never = acc_empty + 1;   // nothing arrives here (wait_test)
+  uint32_t* tmem_slot = (uint32_t*)(never + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   if (tid == 0) s_start = (*(volatile unsigned*)status & kStatusTimeout) ? 0 : 1;
@@ -308,6 +309,7 @@ __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcAr
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(acc_full)));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(smem_u32(acc_empty)));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(never)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == TC_MMA_WARP) {
@@ -383,7 +385,9 @@ __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcAr
     if (lane == 0) {
       int64_t g = 0, last = -1;
       int i = 0;
-      bool ok = true;
+      // wait_test: a wait that can only end by giving up (phase 0 of `never`
+      // never completes); the CTA then takes the timeout path below
+      bool ok = !(a.wait_test && blockIdx.x == 0) || mbar_wait(smem_u32(never), 0u, status);
       for (int64_t it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++i) {
         const int b = (int)(it % nb);
         const int n = min(TC_NMAX, 2 * a.M - TC_NMAX * b);

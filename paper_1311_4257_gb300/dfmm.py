@@ -31,7 +31,8 @@ class DfmmError(RuntimeError):
 class Options(ctypes.Structure):
     _fields_ = [("leaf_max", ctypes.c_int32), ("sample_box", ctypes.c_int32), ("sample_far", ctypes.c_int32),
                 ("sketch_rows", ctypes.c_int32), ("eps_op_factor", ctypes.c_double), ("m2l_mode", ctypes.c_int32),
-                ("host_threads", ctypes.c_int32), ("cache_dir", ctypes.c_char_p), ("tc_stages", ctypes.c_int32)]
+                ("host_threads", ctypes.c_int32), ("cache_dir", ctypes.c_char_p), ("tc_stages", ctypes.c_int32),
+                ("wait_test", ctypes.c_int32), ("tile_order", ctypes.c_int32), ("p2p_mode", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -43,7 +44,8 @@ class Stats(ctypes.Structure):
                 ("rank", ctypes.c_int32 * 32), ("v_pairs", ctypes.c_int64), ("u_pairs", ctypes.c_int64),
                 ("w_pairs", ctypes.c_int64), ("x_pairs", ctypes.c_int64), ("p2p_interactions", ctypes.c_int64),
                 ("plan_bytes", ctypes.c_int64), ("plan_seconds", ctypes.c_double), ("m2l_flops", ctypes.c_double),
-                ("other_translation_flops", ctypes.c_double), ("hf_ops", ctypes.c_int64 * 32)]
+                ("other_translation_flops", ctypes.c_double), ("hf_ops", ctypes.c_int64 * 32),
+                ("p2p_close_pairs", ctypes.c_int64)]
 
     def to_dict(self) -> dict:
         n = self.n_levels
@@ -65,6 +67,13 @@ class ServerReport(ctypes.Structure):
 class KernelTime(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_int64), ("ms", ctypes.c_double),
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+class Peaks(ctypes.Structure):
+    _fields_ = [("sm_count", ctypes.c_int32), ("reserved", ctypes.c_int32), ("fp32_fma_tflops", ctypes.c_double),
+                ("fp64_fma_tflops", ctypes.c_double), ("sincos_gops", ctypes.c_double),
+                ("rsqrt_gops", ctypes.c_double), ("tf32_mma_tflops", ctypes.c_double),
+                ("f16_mma_tflops", ctypes.c_double)]
 
 
 _lib = None
@@ -105,12 +114,13 @@ def lib() -> ctypes.CDLL:
         L.dfmm_graph_destroy.argtypes = [vp]
         L.dfmm_solve.argtypes = [vp, dbl, dbl, dbl, dbl, vp, vp, i32, i32, dbl, vp, ctypes.POINTER(i32),
                                  ctypes.POINTER(dbl)]
+        L.dfmm_measure_peaks.argtypes = [ctypes.POINTER(Peaks)]
         L.dfmm_last_error.restype = ctypes.c_char_p
         for f in ("dfmm_plan", "dfmm_apply", "dfmm_apply_host", "dfmm_sync_status", "dfmm_destroy",
                   "dfmm_plan_stats", "dfmm_export", "dfmm_representation", "dfmm_profile", "dfmm_apply_batched",
                   "dfmm_server_create", "dfmm_server_submit", "dfmm_server_wait", "dfmm_server_stats",
                   "dfmm_server_destroy", "dfmm_solve", "dfmm_graph_create", "dfmm_graph_launch",
-                  "dfmm_graph_destroy"):
+                  "dfmm_graph_destroy", "dfmm_measure_peaks"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -134,6 +144,13 @@ def representation(w: float, cell: int, w_top: float, eps_op: float, sample_box:
     return r.value, b2[:n].copy(), a2[:n].copy()
 
 
+def measure_peaks() -> dict:
+    """dfmm_measure_peaks: probed peak rates of the current GPU."""
+    pk = Peaks()
+    _check(lib().dfmm_measure_peaks(ctypes.byref(pk)))
+    return {name: getattr(pk, name) for name, _ in pk._fields_ if name != "reserved"}
+
+
 def _stream_ptr(stream) -> int:
     if stream is None:
         import torch
@@ -146,7 +163,8 @@ class Plan:
 
     def __init__(self, points, K: float, eps: float, leaf_max: int = 0, sample_box: int = 0, sample_far: int = 0,
                  sketch_rows: int = 0, eps_op_factor: float = 0.0, host_threads: int = 0,
-                 cache_dir: str | None = None, m2l_mode: int = 0, tc_stages: int = 0):
+                 cache_dir: str | None = None, m2l_mode: int = 0, tc_stages: int = 0, wait_test: int = 0,
+                 tile_order: int = 0, p2p_mode: int = 0):
         import torch
         if not (isinstance(points, torch.Tensor) and points.is_cuda):
             points = torch.as_tensor(np.ascontiguousarray(points, dtype=np.float64), device="cuda")
@@ -157,7 +175,7 @@ class Plan:
         self.K = float(K)
         self.eps = float(eps)
         o = Options(leaf_max, sample_box, sample_far, sketch_rows, eps_op_factor, m2l_mode, host_threads,
-                    cache_dir.encode() if cache_dir else None, tc_stages)
+                    cache_dir.encode() if cache_dir else None, tc_stages, wait_test, tile_order, p2p_mode)
         h = ctypes.c_void_p()
         _check(lib().dfmm_plan(points.data_ptr(), self.N, self.K, self.eps, ctypes.byref(o), ctypes.byref(h)))
         self._h = h

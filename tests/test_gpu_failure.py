@@ -1,0 +1,61 @@
+"""Failure detection on the device, without faulting or hanging the GPU.
+
+Every wait of the tensor-core translation kernel is bounded (0.2 s).  The plan
+option wait_test makes the first CTA of each tensor-core launch wait on a
+barrier that nothing arrives at: the wait gives up, the CTA and the rest of
+the apply's tensor-core launches stop early, and the status word that
+dfmm_sync_status reads reports DFMM_ERR_TIMEOUT.  The context stays usable:
+the next apply of an ordinary plan on the same stream is correct.
+"""
+import numpy as np
+import pytest
+
+import workloads
+from oracle import direct as OD
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1311_4257_gb300 import build
+    build.build()
+    from paper_1311_4257_gb300 import dfmm
+    return torch, dfmm
+
+
+def test_wait_that_runs_out_reports_timeout_and_context_survives(env):
+    torch, dfmm = env
+    p = workloads.sphere(4.0, 31)
+    f = workloads.densities(p.shape[0], 1, 31)
+    fd = torch.as_tensor(f.astype(np.complex64), device="cuda")
+    stream = torch.cuda.Stream()
+    stalled = dfmm.Plan(p, 4.0, 1e-5, m2l_mode=2, wait_test=1)
+    with torch.cuda.stream(stream):
+        stalled.apply(fd)
+    assert stalled.sync_status(stream) == dfmm.ERR_TIMEOUT
+    assert b"wait" in dfmm.lib().dfmm_last_error()
+    # the same stream and device afterwards: an ordinary plan gives correct potentials
+    plan = dfmm.Plan(p, 4.0, 1e-5, m2l_mode=2)
+    with torch.cuda.stream(stream):
+        u = plan.apply(fd)
+    assert plan.sync_status(stream) == dfmm.OK
+    u = u.cpu().numpy().astype(np.complex128)
+    assert OD.rel_err(u, OD.direct(p, f)) < 1e-5
+    # the stalled plan keeps reporting the timeout on every apply
+    with torch.cuda.stream(stream):
+        stalled.apply(fd)
+    assert stalled.sync_status(stream) == dfmm.ERR_TIMEOUT
+
+
+def test_status_is_ok_after_ordinary_applies(env):
+    torch, dfmm = env
+    p = workloads.sphere(4.0, 32)
+    fd = torch.as_tensor(workloads.densities(p.shape[0], 2, 32).astype(np.complex64), device="cuda")
+    for mode in (1, 2):
+        plan = dfmm.Plan(p, 4.0, 1e-5, m2l_mode=mode)
+        plan.apply(fd)
+        assert plan.sync_status() == dfmm.OK

@@ -102,11 +102,14 @@ def test_small_sphere_parity():
 
 
 def test_sphere_k8_eps1e6():
-    """Sphere diameter 8, N = 20,106, eps = 1e-6, all targets of the direct sum."""
+    """Sphere diameter 8, N = 20,106 (seed 0), eps = 1e-6, complex128 densities:
+    within eps of the direct sum of Eq. 1 on all 20,106 targets, and within
+    1e-5 of the oracle FMM (automatic form: FP32 CUDA cores below eps 1e-5)."""
     p = workloads.sphere(8.0, 0)
-    e_fmm, e_dir, e_or = _parity(p, 8.0, 1e-6, ntgt=4000)
+    assert p.shape[0] == 20106
+    e_fmm, e_dir, e_or = _parity(p, 8.0, 1e-6)
     assert e_fmm <= 1e-5
-    assert e_dir <= 1e-6 * 2.0, (e_dir, e_or)   # FP32 path at eps = 1e-6: reported, bound 2 eps
+    assert e_dir <= 1e-6, (e_dir, e_or)
 
 
 def test_adaptive_tree_parity():
@@ -141,9 +144,18 @@ def test_degenerate_inputs():
     g = _plan(p, 4.0, 1e-6)
     u = _apply(g, f)
     assert u[0, 1] == u[0, 2]                     # duplicates see the same sources
+    ud = OD.direct(p, f)
     uo = OF.fmm(OF.Plan(p, 4.0, OF.FMMParams(eps=1e-6)), f)
-    assert OD.rel_err(u, uo) < 1e-5
-    assert OD.rel_err(u, OD.direct(p, f)) < 1e-5
+    assert OD.rel_err(u, uo) < 1e-6               # the GPU computes what the oracle computes
+    # A target here sums a handful of far sources, so the potentials carry the
+    # representation's pointwise error, bounded by 20 eps_op = 6 eps (eps_op =
+    # 0.3 eps; the reading on few-source inputs), not the averaged eps of a
+    # surface; the FP64 oracle shows the same error.  With eps_op = 0.1 eps
+    # the bound eps holds here as well.
+    assert OD.rel_err(u, ud) <= 20 * 0.3e-6
+    assert abs(OD.rel_err(u, ud) - OD.rel_err(uo, ud)) < 1e-7
+    u01 = _apply(_plan(p, 4.0, 1e-6, eps_op_factor=0.1), f)
+    assert OD.rel_err(u01, ud) <= 1e-6
 
 
 @pytest.mark.parametrize("case", ["torus", "cube", "ellipsoid"])
@@ -224,3 +236,56 @@ def test_tensor_core_families_one_at_a_time():
         assert 0 < e < e_all * 1.2 + 1e-7, (mask, e, e_all)
     # P2L projection (X lists, only where the LF tree is adaptive) alone
     assert OD.rel_err(_apply(_plan(p, 8.0, 1e-5, m2l_mode=2, tc_stages=16), f), u_fp) < e_all * 1.2 + 1e-7
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("eps,tile_order", [(1e-5, 2), (1e-6, 0)])
+def test_sphere_k16_tensor_cores_against_oracle_fmm(eps, tile_order):
+    """Sphere diameter 16, N = 80,424 (seed 1), tensor-core form, against the
+    oracle FMM element by element on all targets (1e-5 relative 2-norm).
+    Reaches the w = 4 HF level, and: at eps 1e-5 the operator-order tile path
+    (forced by tile_order 2; full-size stages take it when their operators
+    exceed 64 MB); at eps 1e-6 ranks above 128, i.e. tiles of two N blocks
+    (2 R > 256 real outputs)."""
+    p = workloads.sphere(16.0, 1)
+    assert p.shape[0] == 80424
+    f = workloads.densities(p.shape[0], 1, 16)
+    g = _plan(p, 16.0, eps, m2l_mode=2, tile_order=tile_order)
+    st = g.stats()
+    l4 = st["level_w1"] - 2                      # the level of width 4
+    assert st["hf_pairs"][l4] > 0 and st["level_hf_top"] == l4
+    if eps < 1e-5:
+        assert max(st["rank"]) > 128
+    u = _apply(g, f)
+    o = OF.Plan(p, 16.0, OF.FMMParams(eps=eps))
+    uo = OF.fmm(o, f)
+    assert OD.rel_err(u, uo) <= 1e-5
+    # against Eq. 1: eps, plus the split's own error at eps 1e-6 (the automatic
+    # form takes the FP32 CUDA cores there; the split adds < 5e-6 against them)
+    t = np.random.default_rng(1016).choice(p.shape[0], 300, replace=False)
+    assert OD.rel_err(u[:, t], OD.direct(p, f, t)) <= max(eps, 5e-6)
+
+
+def test_fp32_near_field_matches_double_float_form():
+    """The FP32 near field (p2p_mode 2) with its exact
+    close-pair corrections against the double-float form (p2p_mode 1) and the
+    direct sum of Eq. 1, on the K = 8 sphere and on points with exact
+    duplicates and near-duplicates (1e-4 and 1e-6 apart, across leaf faces)."""
+    p = workloads.sphere(8.0, 0)
+    f = workloads.densities(p.shape[0], 2, 21)
+    g2 = _plan(p, 8.0, 1e-5, p2p_mode=2)
+    assert g2.stats()["p2p_close_pairs"] > p.shape[0]
+    u2 = _apply(g2, f)
+    u1 = _apply(_plan(p, 8.0, 1e-5, p2p_mode=1), f)
+    assert OD.rel_err(u2, u1) < 1e-6
+    t = np.arange(0, p.shape[0], 5)
+    assert OD.rel_err(u2[:, t], OD.direct(p, f, t)) <= 1e-5
+    rng = np.random.default_rng(22)
+    q = rng.uniform(-1.9, 1.9, (3000, 3))
+    q[:20] = q[20:40]                                   # exact duplicates
+    q[40:60] = q[60:80] + 1e-4 * rng.standard_normal((20, 3))
+    q[80:90] = np.array([0.0, 0.3, -0.7]) + 1e-6 * rng.standard_normal((10, 3))   # straddle x = 0
+    fq = workloads.densities(q.shape[0], 1, 23)
+    uq = _apply(_plan(q, 4.0, 1e-5, p2p_mode=2), fq)
+    assert OD.rel_err(uq, OD.direct(q, fq)) <= 1e-5
+    assert OD.rel_err(uq, _apply(_plan(q, 4.0, 1e-5, p2p_mode=1), fq)) < 1e-6
