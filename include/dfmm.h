@@ -79,11 +79,12 @@ typedef struct {
                               stay in L2), else by operator (each read from DRAM once); 1 = always
                               by target block; 2 = always by operator.  The result is the same up
                               to the order of the floating-point additions. */
-  int32_t p2p_mode;        /* [0] near-field form: 0 = automatic (1);
+  int32_t p2p_mode;        /* [0] near-field form: 0 = automatic (2 if eps >= 1e-5, else 1);
                               1 = double-float box-local coordinates; 2 = FP32 coordinates, with
                               the pairs closer than min(0.5, 1e-6 / eps) wavelengths corrected
                               exactly (listed at plan time).  Form 2 falls back to 1 when two
-                              distinct points round to the same FP32 coordinates. */
+                              distinct points round to the same FP32 coordinates, when N >= 2^25,
+                              or when a leaf has more than 127 near leaves. */
 } dfmm_options;
 
 /* Build a plan (Sec. 2.2 octree, lists, Eq. 2 representations and the

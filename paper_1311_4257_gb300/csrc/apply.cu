@@ -17,6 +17,8 @@
 //  * p2p_kernel: the near field (U lists) in FP32 on box-local coordinates.
 #include "apply.h"
 
+#include <type_traits>
+
 namespace dfmm {
 
 namespace {
@@ -129,9 +131,17 @@ __global__ void permute_out_kernel(const float2* __restrict__ us, const int32_t*
   u[(int64_t)r * N + perm[k]] = us[e];
 }
 
+// x rounded to the nearest integer (ties to even) for |x| < 2^22: adding
+// 1.5 * 2^23 moves x into the binade where the FP32 spacing is 1.  Two adds
+// on the FMA pipe, where rintf would take a slot of the special-function unit
+// that the sine, cosine and reciprocal square root already saturate.
+__device__ __forceinline__ float round_near(float x) {
+  return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
+}
+
 // exp(2 pi i phase) / d with phase reduced to [-1/2, 1/2]
 __device__ __forceinline__ float2 green_phase(float phase, float inv_d) {
-  float ph = phase - rintf(phase);
+  float ph = phase - round_near(phase);
   float s, c;
   __sincosf(6.28318530717958647f * ph, &s, &c);
   return make_float2(c * inv_d, s * inv_d);
@@ -427,9 +437,8 @@ __global__ __launch_bounds__(P2P_THREADS) void p2p_kernel(P2PArgs a) {
         const int nb = (int)(u1 - ub < P2P_LEAVES ? u1 - ub : P2P_LEAVES);
         __syncthreads();   // the previous batch has been consumed
         if (threadIdx.x < nb) {
-          const int4 e = a.u_src[ub + threadIdx.x];
-          su[threadIdx.x] = e;
-          ssh[threadIdx.x] = a.shifts[e.z];
+          su[threadIdx.x] = a.u_src[ub + threadIdx.x];
+          ssh[threadIdx.x] = a.u_shift[ub + threadIdx.x];
         }
         __syncthreads();
         if (threadIdx.x < 32) {   // exclusive prefix of the leaf sizes
@@ -529,7 +538,6 @@ __global__ __launch_bounds__(P2P_THREADS) void p2p_kernel(P2PArgs a) {
 
 constexpr int PF_THREADS = 128;
 constexpr int PF_CHUNK = 512;
-constexpr int PF_LEAVES = 64;
 
 // The FP32 form's kernel value for one pair: target x and source y in the target
 // leaf's frame.  Every rounding is explicit, so the close-pair pass reproduces
@@ -540,7 +548,7 @@ __device__ __forceinline__ float2 g32(float xx, float xy, float xz, float4 y) {
   const float r2 = __fmaf_rn(dx, dx, __fmaf_rn(dy, dy, __fmul_rn(dz, dz)));
   const float inv = guarded ? (r2 > 0.f ? rsqrtf(r2) : 0.f) : rsqrtf(r2);
   const float d = __fmul_rn(r2, inv);
-  const float ph = __fsub_rn(d, rintf(d));
+  const float ph = __fsub_rn(d, round_near(d));
   float sn, cs;
   __sincosf(__fmul_rn(6.28318530717958647f, ph), &sn, &cs);
   return make_float2(__fmul_rn(cs, inv), __fmul_rn(sn, inv));
@@ -559,17 +567,23 @@ __global__ __launch_bounds__(PF_THREADS) void p2p_fast_kernel(P2PArgs a) {
   __shared__ float4 sy[PF_CHUNK];
   __shared__ float2 sf[PF_CHUNK][NR];
   __shared__ float2 red[PF_THREADS][2][NR];
-  __shared__ int4 su[PF_LEAVES];
-  __shared__ float4 ssh[PF_LEAVES];
-  __shared__ int soff[PF_LEAVES + 1];
+  __shared__ float4 stab[128];   // shift of each entry of the leaf's list
   const int2 lr = a.leaf_range[blockIdx.x];
   const int64_t u0 = a.u_off[blockIdx.x], u1 = a.u_off[blockIdx.x + 1];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // the leaf's list: the flat staging list and the entry offsets are precomputed
+  const int4 e0 = a.u_src[u0], el = a.u_src[u1 - 1];
+  const int total = el.z + el.y - e0.z;
+  const int self_end = e0.w ? e0.y : 0;   // staged indices of the own leaf's points
+  for (int t = threadIdx.x; t < (int)(u1 - u0); t += PF_THREADS) stab[t] = a.u_shift[u0 + t];
   for (int t0 = 0; t0 < lr.y; t0 += 2 * PF_THREADS) {
     const int nt = min(2 * PF_THREADS, lr.y - t0);
     const int nth = (nt + 1) >> 1;
-    const int ngrp = PF_THREADS / nth;
-    const int ti = threadIdx.x % nth, grp = threadIdx.x / nth;
+    // thread -> (group, target pair) without integer division: the operands are
+    // below 256, so the correctly rounded reciprocal leaves a margin of 1 / 256
+    const float rth = __frcp_rn((float)nth);
+    const int ngrp = (int)(((float)PF_THREADS + 0.5f) * rth);
+    const int grp = (int)(((float)threadIdx.x + 0.5f) * rth), ti = threadIdx.x - grp * nth;
+    const float rgrp = __frcp_rn((float)ngrp);
     const bool active = grp < ngrp;
     const int i1 = ti + nth < nt ? ti + nth : ti;   // an odd count repeats the last target
     const float4 x0 = a.pts[lr.x + t0 + ti];
@@ -579,81 +593,50 @@ __global__ __launch_bounds__(PF_THREADS) void p2p_fast_kernel(P2PArgs a) {
       float2 acc0[NR], acc1[NR];
 #pragma unroll
       for (int k = 0; k < NR; ++k) acc0[k] = acc1[k] = make_float2(0.f, 0.f);
-      for (int64_t ub = u0; ub < u1; ub += PF_LEAVES) {
-        const int nb = (int)(u1 - ub < PF_LEAVES ? u1 - ub : PF_LEAVES);
-        __syncthreads();   // the previous batch has been consumed
-        if (threadIdx.x < nb) {
-          const int4 e = a.u_src[ub + threadIdx.x];
-          su[threadIdx.x] = e;
-          ssh[threadIdx.x] = a.shifts[e.z];
+      for (int c0 = 0; c0 < total; c0 += PF_CHUNK) {
+        const int fill = min(PF_CHUNK, total - c0);
+        __syncthreads();   // the previous chunk (and the previous pass's sums) are consumed
+        // one thread per staged source: its point, shifted into this leaf's frame
+        for (int q = threadIdx.x; q < fill; q += PF_THREADS) {
+          const uint32_t v = a.flat[e0.z + c0 + q];
+          const int j = (int)(v & 0x1FFFFFFu);
+          sy[q] = shifted(a.pts[j], stab[v >> 25]);
+#pragma unroll
+          for (int k = 0; k < NR; ++k)
+            sf[q][k] = k < nr ? a.fs[(int64_t)j * a.nrhs + r0 + k] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        if (threadIdx.x < 32) {   // exclusive prefix of the leaf sizes
-          int v0 = lane < nb ? su[lane].y : 0;
-          int v1 = lane + 32 < nb ? su[lane + 32].y : 0;
+        if (active) {
+          // the own leaf's points (staged first) take the guarded form, spread
+          // over the groups so that the lanes of a warp stay on one path; the
+          // rest is split into contiguous shares
+          const int self_hi = min(max(self_end - c0, 0), fill);
+          const int per = (int)(((float)(fill - self_hi + ngrp) - 0.5f) * rgrp);   // ceil((fill - self_hi) / ngrp)
+          const int jlo = min(fill, self_hi + grp * per), jhi = min(fill, jlo + per);
+          auto body = [&](int j, auto guard) {
+            const float4 y = sy[j];
+            constexpr bool G = decltype(guard)::value;
+            const float2 g0 = g32<G>(x0.x, x0.y, x0.z, y), g1 = g32<G>(x1.x, x1.y, x1.z, y);
 #pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xffffffffu, v0, o);
-            int w = __shfl_up_sync(0xffffffffu, v1, o);
-            if (lane >= o) { v0 += t; v1 += w; }
-          }
-          v1 += __shfl_sync(0xffffffffu, v0, 31);
-          soff[lane + 1] = v0;
-          soff[lane + 33] = v1;
-          if (lane == 0) soff[0] = 0;
-        }
-        __syncthreads();
-        const int total = soff[nb];
-        const int self_end = (ub == u0 && su[0].w) ? soff[1] : 0;   // staged indices of the own leaf
-        for (int c0 = 0; c0 < total; c0 += PF_CHUNK) {
-          const int fill = min(PF_CHUNK, total - c0);
-          if (c0 > 0) __syncthreads();
-          // one warp per U entry: its points, shifted into this leaf's frame
-          for (int e = warp; e < nb; e += PF_THREADS / 32) {
-            const int lo = max(soff[e], c0), hi = min(soff[e + 1], c0 + fill);
-            const int base = su[e].x - soff[e];
-            const float4 sh = ssh[e];
-            for (int q = lo + lane; q < hi; q += 32) {
-              const int j = base + q;
-              sy[q - c0] = shifted(a.pts[j], sh);
-#pragma unroll
-              for (int k = 0; k < NR; ++k)
-                sf[q - c0][k] = k < nr ? a.fs[(int64_t)j * a.nrhs + r0 + k] : make_float2(0.f, 0.f);
+            for (int k = 0; k < NR; ++k) {
+              const float2 f = sf[j][k];
+              acc0[k].x = fmaf(g0.x, f.x, fmaf(-g0.y, f.y, acc0[k].x));
+              acc0[k].y = fmaf(g0.x, f.y, fmaf(g0.y, f.x, acc0[k].y));
+              acc1[k].x = fmaf(g1.x, f.x, fmaf(-g1.y, f.y, acc1[k].x));
+              acc1[k].y = fmaf(g1.x, f.y, fmaf(g1.y, f.x, acc1[k].y));
             }
+          };
+          for (int j = grp; j < self_hi; j += ngrp) body(j, std::true_type());
+          int j = jlo;
+          for (; j + 3 < jhi; j += 4) {
+            body(j, std::false_type());
+            body(j + 1, std::false_type());
+            body(j + 2, std::false_type());
+            body(j + 3, std::false_type());
           }
-          __syncthreads();
-          if (active) {
-            const int self_hi = min(max(self_end - c0, 0), fill);
-            int j = grp;
-            for (; j < self_hi; j += ngrp) {
-              const float4 y = sy[j];
-              const float2 g0 = g32<true>(x0.x, x0.y, x0.z, y), g1 = g32<true>(x1.x, x1.y, x1.z, y);
-#pragma unroll
-              for (int k = 0; k < NR; ++k) {
-                const float2 f = sf[j][k];
-                acc0[k].x = fmaf(g0.x, f.x, fmaf(-g0.y, f.y, acc0[k].x));
-                acc0[k].y = fmaf(g0.x, f.y, fmaf(g0.y, f.x, acc0[k].y));
-                acc1[k].x = fmaf(g1.x, f.x, fmaf(-g1.y, f.y, acc1[k].x));
-                acc1[k].y = fmaf(g1.x, f.y, fmaf(g1.y, f.x, acc1[k].y));
-              }
-            }
-#pragma unroll 4
-            for (; j < fill; j += ngrp) {
-              const float4 y = sy[j];
-              const float2 g0 = g32<false>(x0.x, x0.y, x0.z, y), g1 = g32<false>(x1.x, x1.y, x1.z, y);
-#pragma unroll
-              for (int k = 0; k < NR; ++k) {
-                const float2 f = sf[j][k];
-                acc0[k].x = fmaf(g0.x, f.x, fmaf(-g0.y, f.y, acc0[k].x));
-                acc0[k].y = fmaf(g0.x, f.y, fmaf(g0.y, f.x, acc0[k].y));
-                acc1[k].x = fmaf(g1.x, f.x, fmaf(-g1.y, f.y, acc1[k].x));
-                acc1[k].y = fmaf(g1.x, f.y, fmaf(g1.y, f.x, acc1[k].y));
-              }
-            }
-          }
+          for (; j < jhi; ++j) body(j, std::false_type());
         }
       }
-      __syncthreads();
 #pragma unroll
       for (int k = 0; k < NR; ++k) {
         red[threadIdx.x][0][k] = active ? acc0[k] : make_float2(0.f, 0.f);
@@ -663,7 +646,6 @@ __global__ __launch_bounds__(PF_THREADS) void p2p_fast_kernel(P2PArgs a) {
       for (int tt = threadIdx.x; tt < nt; tt += PF_THREADS) {
         const int th = tt < nth ? tt : tt - nth, slot = tt < nth ? 0 : 1;
         const int64_t i = lr.x + t0 + tt;
-        const int c0 = a.close_off[i], c1 = a.close_off[i + 1];
         for (int k = 0; k < nr; ++k) {
           float2 sum = make_float2(0.f, 0.f);
           for (int g = 0; g < ngrp; ++g) {
@@ -671,19 +653,31 @@ __global__ __launch_bounds__(PF_THREADS) void p2p_fast_kernel(P2PArgs a) {
             sum.x += v.x;
             sum.y += v.y;
           }
-          for (int c = c0; c < c1; ++c) {   // exact corrections of the close pairs
-            const float2 w = a.close_w[c];
-            const float2 f = a.fs[(int64_t)a.close_j[c] * a.nrhs + r0 + k];
-            sum.x = fmaf(w.x, f.x, fmaf(-w.y, f.y, sum.x));
-            sum.y = fmaf(w.x, f.y, fmaf(w.y, f.x, sum.y));
-          }
-          float2* uu = a.us + i * a.nrhs + r0 + k;
-          const float2 o = *uu;
-          *uu = make_float2(o.x + sum.x, o.y + sum.y);
+          red_add2((float*)(a.us + i * a.nrhs + r0 + k), sum.x, sum.y);   // no round trip
         }
       }
-      __syncthreads();
     }
+  }
+}
+
+// Exact corrections of the close pairs of the FP32 form, one thread per
+// target point: us[i] += sum_c w_c f[j_c].
+__global__ void p2p_close_apply_kernel(P2PArgs a, int64_t npoints) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npoints) return;
+  const int c0 = a.close_off[i], c1 = a.close_off[i + 1];
+  if (c0 == c1) return;
+  for (int k = 0; k < a.nrhs; ++k) {
+    float2 sum = make_float2(0.f, 0.f);
+    for (int c = c0; c < c1; ++c) {
+      const float2 w = a.close_w[c];
+      const float2 f = a.fs[(int64_t)a.close_j[c] * a.nrhs + k];
+      sum.x = fmaf(w.x, f.x, fmaf(-w.y, f.y, sum.x));
+      sum.y = fmaf(w.x, f.y, fmaf(w.y, f.x, sum.y));
+    }
+    float2* uu = a.us + i * a.nrhs + k;
+    const float2 o = *uu;
+    *uu = make_float2(o.x + sum.x, o.y + sum.y);
   }
 }
 
@@ -701,7 +695,7 @@ __global__ void p2p_close_kernel(P2PArgs a, float delta2, int32_t* cnt, unsigned
     int n = 0;
     for (int64_t e = u0; e < u1; ++e) {
       const int4 ue = a.u_src[e];
-      const float4 sh = a.shifts[ue.z];
+      const float4 sh = a.u_shift[e];
       for (int q = 0; q < ue.y; ++q) {
         const int j = ue.x + q;
         const float4 v = a.pts[j], vl = a.pts_lo[j];
@@ -789,11 +783,13 @@ void launch_p2m_rows(const P2MRowsArgs& a, cudaStream_t s) {
   DFMM_CUDA(cudaGetLastError());
 }
 
-void launch_p2p_fast(const P2PArgs& a, cudaStream_t s) {
+void launch_p2p_fast(const P2PArgs& a, int64_t npoints, cudaStream_t s) {
   if (a.nleaves == 0) return;
   if (a.nrhs == 1) p2p_fast_kernel<1><<<(unsigned)a.nleaves, PF_THREADS, 0, s>>>(a);
   else if (a.nrhs == 2) p2p_fast_kernel<2><<<(unsigned)a.nleaves, PF_THREADS, 0, s>>>(a);
   else p2p_fast_kernel<4><<<(unsigned)a.nleaves, PF_THREADS, 0, s>>>(a);
+  DFMM_CUDA(cudaGetLastError());
+  p2p_close_apply_kernel<<<(unsigned)((npoints + 255) / 256), 256, 0, s>>>(a, npoints);
   DFMM_CUDA(cudaGetLastError());
 }
 

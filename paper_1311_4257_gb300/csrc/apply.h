@@ -118,9 +118,12 @@ struct P2PArgs {
   const int2* leaf_range;    // (first, count) per target leaf
   int64_t nleaves;
   const int64_t* u_off;      // CSR offsets per target leaf
-  const int4* u_src;         // (first, count, shift index, self) per source leaf; the target
+  const int4* u_src;         // (first point, count, offset of its first point in the flat
+                             //   list of all leaves' sources, self) per source leaf; the target
                              //   leaf's own entry comes first, with self = 1
-  const float4* shifts;      // c_src - c_tgt
+  const float4* u_shift;     // c_src - c_tgt per source leaf
+  const uint32_t* flat;      // FP32 form: the staged sources of every leaf in order, point index
+                             //   | (entry within the leaf's list << 25), at the entries' .z
   const float4* pts;         // local (x, y, z, |x|^2), high parts
   const float4* pts_lo;      // low parts of the local coordinates
   const float2* fs;
@@ -133,8 +136,8 @@ struct P2PArgs {
 };
 // Double-float coordinates throughout (any accuracy).
 void launch_p2p(const P2PArgs& a, cudaStream_t s);
-// FP32 coordinates (high parts) throughout, plus the close-pair corrections.
-void launch_p2p_fast(const P2PArgs& a, cudaStream_t s);
+// FP32 coordinates (high parts) throughout, then the close-pair corrections.
+void launch_p2p_fast(const P2PArgs& a, int64_t npoints, cudaStream_t s);
 // Close pairs of the FP32 form: every (target i, source j) of the U lists with
 // FP32 distance below delta and p_j != p_i.  Pass 1 (off == nullptr): counts per
 // target point into cnt[N], and sets *degenerate if two distinct points have FP32

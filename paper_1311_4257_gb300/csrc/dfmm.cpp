@@ -191,6 +191,7 @@ struct dfmm_plan_s {
   int64_t* p2p_off = nullptr;
   int4* p2p_src = nullptr;
   float4* p2p_shift = nullptr;
+  uint32_t* p2p_flat = nullptr;   // FP32 near field: flat staging list
   int32_t* close_off = nullptr;   // FP32 near field: close-pair corrections (CSR per sorted point)
   int32_t* close_j = nullptr;
   float2* close_w = nullptr;
@@ -955,44 +956,50 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
     }
     P->m2p.push_back(g);
   }
-  // P2P lists (U), CSR per target leaf with exact centre offsets
+  // P2P lists (U), CSR per target leaf: per source leaf (first point, count,
+  // offset of its points within the leaf's list, self) and the exact centre
+  // offset c_src - c_tgt (a multiple of the finest half-width, exact in FP32)
   {
-    std::vector<std::vector<int4>> per(leaf_range.size());
-    std::vector<float4> shifts;
-    std::map<std::array<int64_t, 3>, int> shift_id;
-    double unit = LV[nl - 1].w / 2;   // all centre offsets are multiples of this
+    std::vector<std::vector<std::pair<int4, float4>>> per(leaf_range.size());
     int64_t inter = 0;
     for (size_t q = 0; q < nU; ++q) {
       int lb = P->U[4 * q], b = P->U[4 * q + 1], la = P->U[4 * q + 2], a = P->U[4 * q + 3];
-      std::array<int64_t, 3> key;
-      double sh[3];
-      for (int d = 0; d < 3; ++d) {
-        sh[d] = center(la, a, d) - center(lb, b, d);
-        key[d] = std::llround(sh[d] / unit);
-      }
-      auto it = shift_id.find(key);
-      int sid;
-      if (it == shift_id.end()) {
-        sid = (int)shifts.size();
-        shift_id[key] = sid;
-        shifts.push_back(make_float4((float)sh[0], (float)sh[1], (float)sh[2], 0.f));
-      } else sid = it->second;
+      float sh[3];
+      for (int d = 0; d < 3; ++d) sh[d] = (float)(center(la, a, d) - center(lb, b, d));
       const int self = (la == lb && a == b) ? 1 : 0;   // the leaf's own entry: may hold coincident points
       auto& lst = per[gleaf.at({lb, b})];
-      lst.push_back(make_int4(LV[la].h_first[a], LV[la].h_count[a], sid, self));
+      lst.push_back({make_int4(LV[la].h_first[a], LV[la].h_count[a], 0, self), make_float4(sh[0], sh[1], sh[2], 0.f)});
       if (self) std::swap(lst.front(), lst.back());   // kept first
       inter += (int64_t)LV[lb].h_count[b] * LV[la].h_count[a];
     }
     std::vector<int64_t> off(leaf_range.size() + 1, 0);
     std::vector<int4> src;
+    std::vector<float4> shifts;
+    // the flat staging list of the FP32 form packs a point index (< 2^25) and
+    // the entry within its leaf's list (< 128) into 32 bits; z = list offset
+    bool flat_ok = N < ((int64_t)1 << 25) && inter < ((int64_t)1 << 62);
+    std::vector<uint32_t> flat;
+    int64_t zacc = 0;
     for (size_t g = 0; g < per.size(); ++g) {
       off[g + 1] = off[g] + (int64_t)per[g].size();
-      src.insert(src.end(), per[g].begin(), per[g].end());
+      if (per[g].size() > 127) flat_ok = false;
+      for (size_t k = 0; k < per[g].size(); ++k) {
+        auto& e = per[g][k];
+        if (zacc >= ((int64_t)1 << 31)) flat_ok = false;
+        e.first.z = (int)std::min<int64_t>(zacc, INT32_MAX);
+        if (flat_ok)
+          for (int q = 0; q < e.first.y; ++q) flat.push_back((uint32_t)(e.first.x + q) | ((uint32_t)k << 25));
+        zacc += e.first.y;
+        src.push_back(e.first);
+        shifts.push_back(e.second);
+      }
     }
     P->p2p_range = upload(leaf_range, ar, s);
     P->p2p_off = upload(off, ar, s);
     P->p2p_src = upload(src, ar, s);
     P->p2p_shift = upload(shifts, ar, s);
+    if (P->opt.p2p_mode == 2 && !flat_ok) P->opt.p2p_mode = 1;   // beyond the packed list: double-float form
+    if (P->opt.p2p_mode == 2) P->p2p_flat = upload(flat, ar, s);
     P->stats.p2p_interactions = inter;
     // FP32 form of the near field: its close pairs and their exact corrections
     // (the pairs closer than delta = 1e-6 / eps, at most 0.5; the FP32
@@ -1003,7 +1010,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
       pa.nleaves = P->n_leaves;
       pa.u_off = P->p2p_off;
       pa.u_src = P->p2p_src;
-      pa.shifts = P->p2p_shift;
+      pa.u_shift = P->p2p_shift;
       pa.pts = P->pts_local;
       pa.pts_lo = P->pts_lo;
       const float delta = (float)std::min(0.5, 1e-6 / P->eps);
@@ -1359,7 +1366,8 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
     a.nleaves = P->n_leaves;
     a.u_off = P->p2p_off;
     a.u_src = P->p2p_src;
-    a.shifts = P->p2p_shift;
+    a.u_shift = P->p2p_shift;
+    a.flat = P->p2p_flat;
     a.pts = P->pts_local;
     a.pts_lo = P->pts_lo;
     a.fs = W->fs;
@@ -1368,7 +1376,7 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
     a.close_off = P->close_off;
     a.close_j = P->close_j;
     a.close_w = P->close_w;
-    if (P->opt.p2p_mode == 2) launch_p2p_fast(a, s);
+    if (P->opt.p2p_mode == 2) launch_p2p_fast(a, N, s);
     else launch_p2p(a, s);
   });
   R.launch(F_PERMUTE, 0.0, 20.0 * N * nrhs, [&] { launch_permute_out(W->us, P->perm, N, nrhs, u, s); });
@@ -1568,9 +1576,9 @@ int dfmm_plan(const double* points, int64_t N, double K, double eps, const dfmm_
     if (o.wait_test < 0 || o.wait_test > 1) return fail(DFMM_ERR_INVALID, "wait_test must be 0 or 1");
     if (o.tile_order < 0 || o.tile_order > 2) return fail(DFMM_ERR_INVALID, "tile_order must be 0, 1 or 2");
     if (o.p2p_mode < 0 || o.p2p_mode > 2) return fail(DFMM_ERR_INVALID, "p2p_mode must be 0, 1 or 2");
-    // automatic near field: double-float coordinates (the FP32 form with
-    // close-pair corrections is selected explicitly)
-    if (o.p2p_mode == 0) o.p2p_mode = 1;
+    // automatic near field: FP32 coordinates with exact close-pair
+    // corrections for eps >= 1e-5, double-float coordinates below
+    if (o.p2p_mode == 0) o.p2p_mode = eps >= 1e-5 ? 2 : 1;
     std::unique_ptr<dfmm_plan_s> P(new dfmm_plan_s());
     DFMM_CUDA(cudaGetDevice(&P->device));
     P->N = N;

@@ -267,7 +267,7 @@ def test_sphere_k16_tensor_cores_against_oracle_fmm(eps, tile_order):
 
 
 def test_fp32_near_field_matches_double_float_form():
-    """The FP32 near field (p2p_mode 2) with its exact
+    """The FP32 near field (p2p_mode 2, automatic at eps >= 1e-5) with its exact
     close-pair corrections against the double-float form (p2p_mode 1) and the
     direct sum of Eq. 1, on the K = 8 sphere and on points with exact
     duplicates and near-duplicates (1e-4 and 1e-6 apart, across leaf faces)."""
