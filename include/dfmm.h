@@ -85,6 +85,16 @@ typedef struct {
                               exactly (listed at plan time).  Form 2 falls back to 1 when two
                               distinct points round to the same FP32 coordinates, when N >= 2^25,
                               or when a leaf has more than 127 near leaves. */
+  int32_t tc_layout;       /* [0] tensor-core translations (m2l_mode 2): 0 = split-complex form
+                              (Re y = Tr xr - Ti xi, Im y = Ti xr + Tr xi as four real products;
+                              ranks padded to 16) wherever the target rank is at most 128, the
+                              real-block form elsewhere; 1 = the real-block form [[Tr, -Ti],
+                              [Ti, Tr]] everywhere (ranks padded to 8). */
+  int32_t tc_accumulate;   /* [0] split-complex form: 0 = the hi*hi terms and the cross terms in
+                              separate tensor-memory accumulators (one tile at a time); 1 = one
+                              accumulator per component, two tensor-memory buffers, so that a
+                              tile's MMAs overlap the previous tile's epilogue (faster; the cross
+                              terms then take the large terms' accumulation truncation). */
 } dfmm_options;
 
 /* Build a plan (Sec. 2.2 octree, lists, Eq. 2 representations and the

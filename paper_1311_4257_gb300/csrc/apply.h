@@ -53,6 +53,23 @@ bool gemm_tc_supported(int M, int Kd);
 int64_t tc_image_elems(int M, int Kd, int nops);
 void build_tc_image(const float2* ops, int M, int Kd, int nops, __half* img, float* scale, cudaStream_t s);
 void launch_split(const float2* x, int64_t rows, int ld, __half* hi, __half* lo, float* scale, cudaStream_t s);
+// scale[op] = smallest power of two >= max |entry| of operator op (per_op complex entries each)
+void compute_op_scales(const float2* ops, int64_t per_op, int nops, float* scale, cudaStream_t s);
+
+// Split-complex tensor-core form (m2l_cx.cu): Re y = Tr xr - Ti xi, Im y =
+// Ti xr + Tr xi as four real GEMMs with N = M (target rank, a multiple of 16,
+// at most 128) and K = Kd (a multiple of 16); operator image of Tr and Ti
+// (build_cx_image) and source rows split into real and imaginary halves
+// (launch_split_cx, rank r = row length in complex values).  Tiles hold up to
+// gemm_cx_columns() columns.
+bool gemm_cx_supported(int M, int Kd);
+int gemm_cx_columns();
+int64_t cx_image_elems(int M, int Kd, int nops);
+void build_cx_image(const float2* ops, int M, int Kd, int nops, __half* img, float* scale, cudaStream_t s);
+void launch_split_cx(const float2* x, int64_t rows, int r, __half* hi, __half* lo, float* scale, cudaStream_t s);
+// one_acc: one accumulator per component, double-buffered tensor memory (faster,
+// the cross terms accumulate with the large terms' truncation)
+void launch_gemm_stage_cx(const GemmArgs& a, const TcArgs& t, unsigned* status, bool one_acc, cudaStream_t s);
 
 // Permutes: fs[k][rhs] = f[rhs][perm[k]];  u[rhs][perm[k]] = us[k][rhs].
 void launch_permute_in(const float2* f, const int32_t* perm, int64_t N, int nrhs, float2* fs, cudaStream_t s);

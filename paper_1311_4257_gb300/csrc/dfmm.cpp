@@ -538,7 +538,9 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
   for (int l = (has_hf ? P->l_top : P->l_lf0); l < nl; ++l) {
     int rmax = 0;
     for (int c : level_cells[l]) rmax = std::max(rmax, P->reps->get(LV[l].w, c).r);
-    int R = round_up(std::max(rmax, 8), 8);
+    // ranks padded to 8; to 16 for the split-complex tensor-core form (the MMA's N and K steps)
+    const int pad = (P->opt.m2l_mode == 2 && P->opt.tc_layout != 1) ? 16 : 8;
+    int R = round_up(std::max(rmax, pad), pad);
     if (R > 256) throw Error(DFMM_ERR_UNSUPPORTED, "representation rank above 256");
     if (l <= P->l1) P->hf[l].R = R;
     else { P->lf[l].R = R; P->lf[l].r = rmax; }
@@ -1139,6 +1141,12 @@ bool on_tensor_cores(const dfmm_plan_s* P, const GemmPlan& g) {
   return P->opt.m2l_mode == 2 && gemm_tc_supported(g.M, g.Kd) && (P->opt.tc_stages & kTcFamBit[g.fam]) != 0;
 }
 
+// whether a tensor-core stage takes the split-complex form (m2l_cx.cu): target
+// rank at most 128 and ranks that are multiples of 16; else the real-block form
+bool split_complex(const dfmm_plan_s* P, const GemmPlan& g) {
+  return on_tensor_cores(P, g) && P->opt.tc_layout != 1 && gemm_cx_supported(g.M, g.Kd);
+}
+
 // tile_order: 0 = by the 64 MB rule above, 1 = always by target block, 2 = always by operator.
 std::vector<int4> make_tiles(const GemmPlan& g, int nrhs, int cols, int tile_order) {
   const int per = std::max(1, cols / nrhs);
@@ -1199,8 +1207,11 @@ struct Runner {
             int src_key, bool first = false) {
     if (g.npairs == 0) return;
     const bool tc = on_tensor_cores(P, g);
-    const bool split = tc && (src_key < 0 || src_key != split_key);
-    if (tc) split_key = src_key;
+    const bool cx = tc && split_complex(P, g);
+    // the split arrays hold one source buffer in one layout (interleaved or split-complex)
+    const int key = src_key < 0 ? -1 : 2 * src_key + (cx ? 1 : 0);
+    const bool split = tc && (key < 0 || key != split_key);
+    if (tc) split_key = key;
     if (count) { count[0] += split ? 2 : 1; return; }
     auto t = tiles_for(P, W, g, nrhs, tc ? gemm_tc_columns() : 64, s);
     GemmArgs a;
@@ -1220,11 +1231,13 @@ struct Runner {
     if (tc) {
       if (split) {
         ProfScope ps(W, s, F_SPLIT, 0.0, (double)src_rows * nrhs * src_ld * 16);
-        launch_split(src, src_rows * nrhs, src_ld, W->ahi, W->alo, W->ascale, s);
+        if (cx) launch_split_cx(src, src_rows * nrhs, src_ld, W->ahi, W->alo, W->ascale, s);
+        else launch_split(src, src_rows * nrhs, src_ld, W->ahi, W->alo, W->ascale, s);
       }
       ProfScope ps(W, s, g.fam, g.flops_rhs * nrhs, g.bytes_fixed + g.bytes_rhs * nrhs);
       TcArgs targs{g.img, g.op_scale, W->ahi, W->alo, W->ascale};
-      launch_gemm_stage_tc(a, targs, W->status, s);
+      if (cx) launch_gemm_stage_cx(a, targs, W->status, P->opt.tc_accumulate == 1, s);
+      else launch_gemm_stage_tc(a, targs, W->status, s);
     } else {
       ProfScope ps(W, s, g.fam, g.flops_rhs * nrhs, g.bytes_fixed + g.bytes_rhs * nrhs);
       launch_gemm_stage(a, s);
@@ -1470,9 +1483,14 @@ void build_images(dfmm_plan_s* P, cudaStream_t s) {
   for (const GemmPlan* gc : all_gemms(P)) {
     GemmPlan* g = const_cast<GemmPlan*>(gc);
     if (g->npairs == 0 || g->nops == 0 || !on_tensor_cores(P, *g)) continue;
-    g->img = P->ar.alloc<__half>(tc_image_elems(g->M, g->Kd, g->nops));
     g->op_scale = P->ar.alloc<float>(g->nops);
-    build_tc_image(g->ops, g->M, g->Kd, g->nops, g->img, g->op_scale, s);
+    if (split_complex(P, *g)) {
+      g->img = P->ar.alloc<__half>(cx_image_elems(g->M, g->Kd, g->nops));
+      build_cx_image(g->ops, g->M, g->Kd, g->nops, g->img, g->op_scale, s);
+    } else {
+      g->img = P->ar.alloc<__half>(tc_image_elems(g->M, g->Kd, g->nops));
+      build_tc_image(g->ops, g->M, g->Kd, g->nops, g->img, g->op_scale, s);
+    }
   }
   DFMM_CUDA(cudaStreamSynchronize(s));
   P->stats.plan_bytes = (int64_t)P->ar.bytes() + (P->close_keep ? (int64_t)P->close_keep->bytes() : 0);
@@ -1576,6 +1594,8 @@ int dfmm_plan(const double* points, int64_t N, double K, double eps, const dfmm_
     if (o.wait_test < 0 || o.wait_test > 1) return fail(DFMM_ERR_INVALID, "wait_test must be 0 or 1");
     if (o.tile_order < 0 || o.tile_order > 2) return fail(DFMM_ERR_INVALID, "tile_order must be 0, 1 or 2");
     if (o.p2p_mode < 0 || o.p2p_mode > 2) return fail(DFMM_ERR_INVALID, "p2p_mode must be 0, 1 or 2");
+    if (o.tc_layout < 0 || o.tc_layout > 1) return fail(DFMM_ERR_INVALID, "tc_layout must be 0 or 1");
+    if (o.tc_accumulate < 0 || o.tc_accumulate > 1) return fail(DFMM_ERR_INVALID, "tc_accumulate must be 0 or 1");
     // automatic near field: FP32 coordinates with exact close-pair
     // corrections for eps >= 1e-5, double-float coordinates below
     if (o.p2p_mode == 0) o.p2p_mode = eps >= 1e-5 ? 2 : 1;

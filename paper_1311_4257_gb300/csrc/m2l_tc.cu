@@ -43,6 +43,7 @@
 #include <algorithm>
 
 #include "apply.h"
+#include "tcgen05.cuh"
 
 namespace dfmm {
 
@@ -61,115 +62,11 @@ constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
 constexpr int SMEM_BYTES = TC_STAGES * STAGE_BYTES + 1024 + 256;   // stages, alignment, barriers
 constexpr int TMEM_COLS = 512;                     // two accumulators of up to 256 columns
 constexpr int CORE_SBO = (TC_BK / 8) * 128;        // 512 B between 8-row groups
-constexpr unsigned long long WAIT_NS = 200000000ull;    // 0.2 s bound on every wait
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+using namespace tc;
 
-// byte offset of fp16 element (row, k) in one stage tile (canonical K-major, no swizzle)
-__host__ __device__ __forceinline__ uint32_t kmaj_off(int row, int k) {
-  return (uint32_t)((row >> 3) * CORE_SBO + (k >> 3) * 128 + (row & 7) * 16 + (k & 7) * 2);
-}
-
-// shared-memory matrix descriptor: start, LBO = 128 B, SBO = 512 B,
-// descriptor version 1, no swizzle
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)(128u >> 4) << 16;
-  d |= (uint64_t)((uint32_t)CORE_SBO >> 4) << 32;
-  d |= (uint64_t)1u << 46;
-  return d;
-}
-
-// instruction descriptor, kind::f16: D f32, A and B f16, K-major, M = 128
-__device__ __forceinline__ uint32_t idesc_f16(int n) {
-  return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
-}
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Wait for the phase with the given parity to complete.  Gives up (false)
-// after WAIT_NS, or as soon as another CTA has reported a timeout, and then
-// reports the timeout itself.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, unsigned* status) {
-  if (mbar_try_wait(bar, parity)) return true;
-  unsigned long long t0 = globaltimer();
-  while (!mbar_try_wait(bar, parity)) {
-    if (globaltimer() - t0 > WAIT_NS || (*(volatile unsigned*)status & kStatusTimeout)) {
-      atomicOr(status, kStatusTimeout);
-      return false;
-    }
-  }
-  return true;
-}
-
-__device__ __forceinline__ void cp_async16(uint32_t saddr, const void* g) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(g) : "memory");
-}
-// 16 zero bytes (source size 0: nothing is read)
-__device__ __forceinline__ void cp_async16_zero(uint32_t saddr, const void* g) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, 0;" ::"r"(saddr), "l"(g) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-// bulk global -> shared copy of `bytes` (multiple of 16), completing on `bar`
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          d_tmem),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
-}
-
-// 16 lanes x 32 columns of one accumulator (.16x256b, 4 repetitions): thread t
-// gets lane t/4 (r[4j], r[4j+1]) and lane t/4 + 8 (r[4j+2], r[4j+3]) at columns
-// 8j + 2 (t % 4) + {0, 1}
-__device__ __forceinline__ void tmem_ld16x256_x4(uint32_t ta, uint32_t* r) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.16x256b.x4.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(ta));
-}
-
-// fire-and-forget add of two floats to global memory (no value returned)
-__device__ __forceinline__ void red_add2(float* p, float a, float b) {
-  asm volatile("red.relaxed.gpu.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
-}
-
-// smallest power of two >= m (1 for m == 0)
-__device__ __forceinline__ float pow2_above(float m) {
-  if (!(m > 0.f)) return 1.f;
-  int e;
-  frexpf(m, &e);
-  return ldexpf(1.f, e);
-}
-
-__device__ __forceinline__ void split_h(float v, __half& h, __half& l) {
-  h = __float2half_rn(v);
-  l = __float2half_rn(v - __half2float(h));
-}
+// byte offset of fp16 element (row, k) in one stage tile
+__host__ __device__ __forceinline__ uint32_t kmaj(int row, int k) { return tc::kmaj_off(row, k, CORE_SBO); }
 
 // per-operator scale: power of two >= max |entry|
 __global__ void op_scale_kernel(const float2* __restrict__ ops, int64_t per_op, float* __restrict__ scale) {
@@ -217,7 +114,7 @@ __global__ void op_image_kernel(const float2* __restrict__ ops, const float* __r
     }
     __half h, l;
     split_h(v, h, l);
-    const uint32_t off = kmaj_off(row, kk) / 2;
+    const uint32_t off = kmaj(row, kk) / 2;
     hi[off] = h;
     lo[off] = l;
   }
@@ -257,16 +154,6 @@ __global__ void split_kernel(const float* __restrict__ x, int64_t rows, int len,
 }
 
 __device__ __forceinline__ void named_bar_producers() { asm volatile("bar.sync 1, %0;" ::"n"(TC_PRODUCERS) : "memory"); }
-
-// Wait without giving up early on another CTA's report (used only to let a
-// CTA's own copies and MMAs land before it frees its memory); time-limited.
-__device__ __forceinline__ bool mbar_wait_drain(uint32_t bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  unsigned long long t0 = globaltimer();
-  while (!mbar_try_wait(bar, parity))
-    if (globaltimer() - t0 > WAIT_NS) return false;
-  return true;
-}
 
 // Persistent, warp-specialised stage kernel.  Work item = (tile, N block);
 // CTA x takes items x, x + gridDim.x, ...  Roles:
@@ -330,24 +217,43 @@ __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcAr
     // ---------------- producers ----------------
     int64_t g = 0;   // chunks issued by this CTA
     bool ok = true;
-    for (int64_t it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
-      const int4 tile = a.tiles[it / nb];
-      const int b = (int)(it % nb);
-      const int n = min(TC_NMAX, 2 * a.M - TC_NMAX * b);
-      const __half* img = t.img + tile.x * op_elems + (int64_t)b * nchunk * 2 * TC_NMAX * TC_BK;
-      // thread tid copies 16-byte piece (tid & 3) of the hi (tid & 4 == 0) or lo
-      // half-line of rows (tid >> 3) + 16 q: 8 lanes cover one row's chunk, so a
-      // warp's copy touches 4 rows x 2 segments of 64 bytes
-      const int piece = tid & 3, which = (tid >> 2) & 1;
-      const __half* srow[8];
+    // thread tid copies 16-byte piece (tid & 3) of the hi (tid & 4 == 0) or lo
+    // half-line of rows (tid >> 3) + 16 q: 8 lanes cover one row's chunk, so a
+    // warp's copy touches 4 rows x 2 segments of 64 bytes.  The source rows of
+    // the next item (tile record, then pair indices) are loaded while this
+    // item's chunks are issued, off the gather's critical path.
+    const int piece = tid & 3, which = (tid >> 2) & 1;
+    const __half* sarr = (which ? t.src_lo : t.src_hi) + 8 * piece;
+    const int64_t G = gridDim.x;
+    auto load_rows = [&](const int4& tl, int* srcrow) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int row = (tid >> 3) + 16 * q;
-        srow[q] = nullptr;
-        if (row < tile.z * a.nrhs)
-          srow[q] = (which ? t.src_lo : t.src_hi) +
-                    ((int64_t)a.pairs[tile.y + row / a.nrhs].x * a.nrhs + row % a.nrhs) * Kreal + 8 * piece;
+        srcrow[q] = -1;
+        if (row < tl.z * a.nrhs) {
+          if (a.nrhs == 1) srcrow[q] = a.pairs[tl.y + row].x;
+          else srcrow[q] = a.pairs[tl.y + row / a.nrhs].x * a.nrhs + row % a.nrhs;
+        }
       }
+    };
+    int4 tile_n = blockIdx.x < nitems ? a.tiles[blockIdx.x / nb] : make_int4(0, 0, 0, 0);
+    int rows_n[8];
+    load_rows(tile_n, rows_n);
+    int4 tile_nn = blockIdx.x + G < nitems ? a.tiles[(blockIdx.x + G) / nb] : make_int4(0, 0, 0, 0);
+    for (int64_t it = blockIdx.x; it < nitems && ok; it += G) {
+      const int4 tile = tile_n;
+      int rows[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) rows[q] = rows_n[q];
+      tile_n = tile_nn;
+      load_rows(tile_n, rows_n);
+      tile_nn = it + 2 * G < nitems ? a.tiles[(it + 2 * G) / nb] : make_int4(0, 0, 0, 0);
+      const int b = (int)(it % nb);
+      const int n = min(TC_NMAX, 2 * a.M - TC_NMAX * b);
+      const __half* img = t.img + tile.x * op_elems + (int64_t)b * nchunk * 2 * TC_NMAX * TC_BK;
+      const __half* srow[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) srow[q] = rows[q] >= 0 ? sarr + (int64_t)rows[q] * Kreal : nullptr;
       for (int c = 0; c < nchunk; ++c, ++g) {
         const int st = (int)(g % TC_STAGES);
         const int64_t j = g / TC_STAGES;
@@ -362,7 +268,7 @@ __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcAr
         const bool kin = k0 + 8 * piece < Kreal;
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const uint32_t dh = sA + (uint32_t)which * A_BYTES + kmaj_off((tid >> 3) + 16 * q, 8 * piece);
+          const uint32_t dh = sA + (uint32_t)which * A_BYTES + kmaj((tid >> 3) + 16 * q, 8 * piece);
           if (srow[q] && kin)
             cp_async16(dh, srow[q] + k0);
           else
@@ -408,9 +314,9 @@ __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcAr
           for (int s = 0; s < ksteps; ++s) {
             const uint32_t off = 256u * s;
             const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
-            mma_f16(tmem, smem_desc(ah + off), smem_desc(bh + off), idesc, acc);
-            mma_f16(tmem + 256u, smem_desc(ah + off), smem_desc(bl + off), idesc, acc);
-            mma_f16(tmem + 256u, smem_desc(al + off), smem_desc(bh + off), idesc, 1u);
+            mma_f16(tmem, smem_desc(ah + off, CORE_SBO), smem_desc(bh + off, CORE_SBO), idesc, acc);
+            mma_f16(tmem + 256u, smem_desc(ah + off, CORE_SBO), smem_desc(bl + off, CORE_SBO), idesc, acc);
+            mma_f16(tmem + 256u, smem_desc(al + off, CORE_SBO), smem_desc(bh + off, CORE_SBO), idesc, 1u);
           }
           asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                            smem_u32(&empty[st]))
@@ -500,6 +406,12 @@ __global__ __launch_bounds__(TC_THREADS, 1) void gemm_tc_kernel(GemmArgs a, TcAr
 }
 
 }  // namespace
+
+void compute_op_scales(const float2* ops, int64_t per_op, int nops, float* scale, cudaStream_t s) {
+  if (nops == 0) return;
+  op_scale_kernel<<<nops, 256, 0, s>>>(ops, per_op, scale);
+  DFMM_CUDA(cudaGetLastError());
+}
 
 int gemm_tc_columns() { return TC_M; }
 

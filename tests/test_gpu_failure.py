@@ -51,6 +51,21 @@ def test_wait_that_runs_out_reports_timeout_and_context_survives(env):
     assert stalled.sync_status(stream) == dfmm.ERR_TIMEOUT
 
 
+def test_wait_that_runs_out_in_the_real_block_form(env):
+    """The same failure path in the real-block tensor-core kernel (tc_layout 1)."""
+    torch, dfmm = env
+    p = workloads.sphere(4.0, 33)
+    f = workloads.densities(p.shape[0], 1, 33)
+    fd = torch.as_tensor(f.astype(np.complex64), device="cuda")
+    stalled = dfmm.Plan(p, 4.0, 1e-5, m2l_mode=2, tc_layout=1, wait_test=1)
+    stalled.apply(fd)
+    assert stalled.sync_status() == dfmm.ERR_TIMEOUT
+    plan = dfmm.Plan(p, 4.0, 1e-5, m2l_mode=2, tc_layout=1)
+    u = plan.apply(fd)
+    assert plan.sync_status() == dfmm.OK
+    assert OD.rel_err(u.cpu().numpy().astype(np.complex128), OD.direct(p, f)) < 1e-5
+
+
 def test_status_is_ok_after_ordinary_applies(env):
     torch, dfmm = env
     p = workloads.sphere(4.0, 32)

@@ -289,3 +289,27 @@ def test_fp32_near_field_matches_double_float_form():
     uq = _apply(_plan(q, 4.0, 1e-5, p2p_mode=2), fq)
     assert OD.rel_err(uq, OD.direct(q, fq)) <= 1e-5
     assert OD.rel_err(uq, _apply(_plan(q, 4.0, 1e-5, p2p_mode=1), fq)) < 1e-6
+
+
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_split_complex_form_matches_real_block_form(nrhs):
+    """The split-complex tensor-core form (Re y = Tr xr - Ti xi, Im y = Ti xr + Tr xi
+    as four real products, the default for ranks up to 128) against the
+    real-block form [[Tr, -Ti], [Ti, Tr]] (tc_layout 1), the FP32 CUDA-core form
+    and the direct sum of Eq. 1; and its one-accumulator, double-buffered
+    variant (tc_accumulate 1)."""
+    p = workloads.sphere(8.0, 0)
+    f = workloads.densities(p.shape[0], nrhs, 13)
+    u_fp = _apply(_plan(p, 8.0, 1e-5, m2l_mode=1), f)
+    g_cx = _plan(p, 8.0, 1e-5, m2l_mode=2)
+    assert all(r % 16 == 0 for r in g_cx.stats()["rank"])
+    u_cx = _apply(g_cx, f)
+    u_rb = _apply(_plan(p, 8.0, 1e-5, m2l_mode=2, tc_layout=1), f)
+    u_one = _apply(_plan(p, 8.0, 1e-5, m2l_mode=2, tc_accumulate=1), f)
+    assert OD.rel_err(u_cx, u_fp) < 2e-6
+    assert OD.rel_err(u_rb, u_fp) < 2e-6
+    assert OD.rel_err(u_one, u_fp) < 4e-6
+    t = np.arange(0, p.shape[0], 9)
+    ud = OD.direct(p, f, t)
+    for u in (u_cx, u_rb, u_one):
+        assert OD.rel_err(u[:, t], ud) <= 1e-5
