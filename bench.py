@@ -317,7 +317,8 @@ def run_ours(args, wl):
         # the scaled FP16 split issues 3 MMAs (hi hi, hi lo, lo hi) per useful
         # multiply-add; FP16 dense runs at the BF16 rate (measured)
         f16 = pk["bf16_tflops"]
-        roofline = {"kernel": "gemm_tc_kernel (all translation stages)", "bound": "tensor", "achieved": achieved,
+        roofline = {"kernel": "gemm_cx_kernel (all translation stages; split-complex form)", "bound": "tensor",
+                    "achieved": achieved,
                     "peak": f16 / 3, "unit": "TFLOP/s", "frac": achieved / (f16 / 3),
                     "issued_tflops": 3 * achieved, "issued_frac_of_f16_peak": 3 * achieved / f16,
                     "peak_source": "measured bf16 dense %.1f TF/s (FP16 runs at the same rate), / 3 MMAs per "
@@ -326,7 +327,7 @@ def run_ours(args, wl):
         roofline = {"kernel": "gemm_stage_kernel (all translation stages)", "bound": "alu", "achieved": achieved,
                     "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["fp32_tflops"],
                     "peak_source": "FP32 CUDA-core peak, %s" % pk["fp32_source"]}
-    roofline.update({"traffic": traffic_for("gemm_tc_kernel", "m2l_tc.cu+dfmm.cpp", args.workload) if tc else
+    roofline.update({"traffic": traffic_for("gemm_cx_kernel", "m2l_cx.cu+dfmm.cpp", args.workload) if tc else
                      traffic_for("gemm_stage_kernel", "apply.cu+dfmm.cpp", args.workload),
                      "launches_per_step": launches / nprof, "ms_per_launch": g_ms / launches,
                      "flops_per_launch": g_flops / launches, "share_of_step": share})
