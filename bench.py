@@ -394,9 +394,11 @@ def run_ours(args, wl):
 
 
 def run_stage_errors(args, wl):
-    """Error that each translation family's FP16 split adds: one plan per family
-    with only that family on the tensor cores (options.tc_stages), against the
-    FP32 CUDA-core form of the same plan and against the FP64 direct sum."""
+    """Error of the tensor-core splits: for the FP16 split, one plan per translation
+    family with only that family on the tensor cores (options.tc_stages); then every
+    family on the tensor cores with each split (FP16, 3xBF16, 3xTF32).  Each against
+    the FP32 CUDA-core form of the same points and against the FP64 direct sum, with
+    the apply time of each form beside it."""
     import numpy as np
     import torch
     import workloads
@@ -411,20 +413,33 @@ def run_stage_errors(args, wl):
     pool = oracle_pool(p, f)
     t, ref, _ = cpu_oracle_sample(p, f, args.ref_targets or 1600, 1001, pool)
     pool.close()
-    forms = [("fp32_cuda_cores", 1, 0), ("m2l_hf", 2, 1), ("m2l_lf", 2, 2), ("m2m", 2, 4), ("l2l", 2, 8),
-             ("p2l_proj", 2, 16), ("all_tensor_cores", 2, 31)]
+    forms = [("fp32_cuda_cores", dict(m2l_mode=1)),
+             ("fp16_m2l_hf", dict(m2l_mode=2, tc_stages=1)), ("fp16_m2l_lf", dict(m2l_mode=2, tc_stages=2)),
+             ("fp16_m2m", dict(m2l_mode=2, tc_stages=4)), ("fp16_l2l", dict(m2l_mode=2, tc_stages=8)),
+             ("fp16_p2l_proj", dict(m2l_mode=2, tc_stages=16)),
+             ("fp16_all", dict(m2l_mode=2)), ("bf16_all_3xBF16", dict(m2l_mode=2, tc_precision=1)),
+             ("tf32_all_3xTF32", dict(m2l_mode=2, tc_precision=2))]
     out, u32 = {}, None
-    for name, mode, mask in forms:
-        plan = Plan(p, wl["K"], wl["eps"], cache_dir=args.cache_dir, m2l_mode=mode, tc_stages=mask)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, kw in forms:
+        plan = Plan(p, wl["K"], wl["eps"], cache_dir=args.cache_dir, **kw)
         u = plan.apply(fd)
+        for _ in range(2):
+            plan.apply(fd, u)
         torch.cuda.synchronize()
+        e0.record()
+        for _ in range(5):
+            plan.apply(fd, u)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
         u = u.cpu().numpy().astype(np.complex128)
         del plan
         torch.cuda.empty_cache()
         if u32 is None:
             u32 = u
-        out[name] = {"vs_direct_sum_fp64": rel_err(u[:, t], ref), "vs_fp32_form": rel_err(u, u32)}
-    print(json.dumps({"metric": "relative error per translation family on the tensor cores (scaled FP16 hi/lo)",
+        out[name] = {"vs_direct_sum_fp64": rel_err(u[:, t], ref), "vs_fp32_form": rel_err(u, u32), "ms": ms}
+    print(json.dumps({"metric": "relative error of the tensor-core splits (scaled hi / lo: FP16, 3xBF16, 3xTF32)",
                       "workload": wl["desc"], "N": N, "eps": wl["eps"], "direct_sum_targets": int(len(t)),
                       "stages": out}), flush=True)
 

@@ -95,6 +95,11 @@ typedef struct {
                               accumulator per component, two tensor-memory buffers, so that a
                               tile's MMAs overlap the previous tile's epilogue (faster; the cross
                               terms then take the large terms' accumulation truncation). */
+  int32_t tc_precision;    /* [0] element type of the scaled hi / lo split of the tensor-core form:
+                              0 = FP16 (11 + 11 significant bits, kind::f16); 1 = BF16 (8 + 8 bits,
+                              "3xBF16"); 2 = TF32 (11 + 11 bits with an 8-bit exponent, kind::tf32
+                              at half the FP16 rate, "3xTF32").  1 and 2 need tc_layout 0; stages
+                              whose target rank exceeds 128 then run on the FP32 CUDA cores. */
 } dfmm_options;
 
 /* Build a plan (Sec. 2.2 octree, lists, Eq. 2 representations and the

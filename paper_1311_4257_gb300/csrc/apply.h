@@ -64,12 +64,15 @@ void compute_op_scales(const float2* ops, int64_t per_op, int nops, float* scale
 // gemm_cx_columns() columns.
 bool gemm_cx_supported(int M, int Kd);
 int gemm_cx_columns();
-int64_t cx_image_elems(int M, int Kd, int nops);
-void build_cx_image(const float2* ops, int M, int Kd, int nops, __half* img, float* scale, cudaStream_t s);
-void launch_split_cx(const float2* x, int64_t rows, int r, __half* hi, __half* lo, float* scale, cudaStream_t s);
+// kind: element type of the split, 0 = FP16, 1 = BF16, 2 = TF32 (4 bytes)
+int cx_elem_bytes(int kind);
+int64_t cx_image_bytes(int M, int Kd, int nops, int kind);
+void build_cx_image(const float2* ops, int M, int Kd, int nops, void* img, float* scale, int kind, cudaStream_t s);
+void launch_split_cx(const float2* x, int64_t rows, int r, void* hi, void* lo, float* scale, int kind, cudaStream_t s);
 // one_acc: one accumulator per component, double-buffered tensor memory (faster,
 // the cross terms accumulate with the large terms' truncation)
-void launch_gemm_stage_cx(const GemmArgs& a, const TcArgs& t, unsigned* status, bool one_acc, cudaStream_t s);
+void launch_gemm_stage_cx(const GemmArgs& a, const TcArgs& t, unsigned* status, bool one_acc, int kind,
+                          cudaStream_t s);
 
 // Permutes: fs[k][rhs] = f[rhs][perm[k]];  u[rhs][perm[k]] = us[k][rhs].
 void launch_permute_in(const float2* f, const int32_t* perm, int64_t N, int nrhs, float2* fs, cudaStream_t s);

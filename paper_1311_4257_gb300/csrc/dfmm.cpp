@@ -1116,7 +1116,8 @@ Workspace* get_workspace(dfmm_plan_s* P, cudaStream_t s, int nrhs) {
   }
   W->p2l = ar.alloc<float2>(p2l_rows * nrhs);
   if (P->opt.m2l_mode == 2) {
-    int64_t e = max_source_elems(P) * nrhs * 2;
+    // split arrays: 2 values per complex element, 2 bytes each (4 for the TF32 split)
+    int64_t e = max_source_elems(P) * nrhs * 2 * (P->opt.tc_precision == 2 ? 2 : 1);
     W->ahi = ar.alloc<__half>(e);
     W->alo = ar.alloc<__half>(e);
     W->ascale = ar.alloc<float>(max_source_rows(P) * nrhs);
@@ -1138,7 +1139,9 @@ Workspace* get_workspace(dfmm_plan_s* P, cudaStream_t s, int nrhs) {
 // whether a translation stage runs on the tensor cores (m2l_mode 2, ranks padded
 // for the MMA, its family selected by options.tc_stages)
 bool on_tensor_cores(const dfmm_plan_s* P, const GemmPlan& g) {
-  return P->opt.m2l_mode == 2 && gemm_tc_supported(g.M, g.Kd) && (P->opt.tc_stages & kTcFamBit[g.fam]) != 0;
+  // the BF16 and TF32 splits exist in the split-complex form only: other stages stay on the CUDA cores
+  return P->opt.m2l_mode == 2 && gemm_tc_supported(g.M, g.Kd) && (P->opt.tc_stages & kTcFamBit[g.fam]) != 0 &&
+         (P->opt.tc_precision == 0 || gemm_cx_supported(g.M, g.Kd));
 }
 
 // whether a tensor-core stage takes the split-complex form (m2l_cx.cu): target
@@ -1231,12 +1234,12 @@ struct Runner {
     if (tc) {
       if (split) {
         ProfScope ps(W, s, F_SPLIT, 0.0, (double)src_rows * nrhs * src_ld * 16);
-        if (cx) launch_split_cx(src, src_rows * nrhs, src_ld, W->ahi, W->alo, W->ascale, s);
+        if (cx) launch_split_cx(src, src_rows * nrhs, src_ld, W->ahi, W->alo, W->ascale, P->opt.tc_precision, s);
         else launch_split(src, src_rows * nrhs, src_ld, W->ahi, W->alo, W->ascale, s);
       }
       ProfScope ps(W, s, g.fam, g.flops_rhs * nrhs, g.bytes_fixed + g.bytes_rhs * nrhs);
       TcArgs targs{g.img, g.op_scale, W->ahi, W->alo, W->ascale};
-      if (cx) launch_gemm_stage_cx(a, targs, W->status, P->opt.tc_accumulate == 1, s);
+      if (cx) launch_gemm_stage_cx(a, targs, W->status, P->opt.tc_accumulate == 1, P->opt.tc_precision, s);
       else launch_gemm_stage_tc(a, targs, W->status, s);
     } else {
       ProfScope ps(W, s, g.fam, g.flops_rhs * nrhs, g.bytes_fixed + g.bytes_rhs * nrhs);
@@ -1445,7 +1448,7 @@ size_t carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaS
   }
   W.p2l = (float2*)take(p2l_rows * nrhs * 8);
   if (P->opt.m2l_mode == 2) {
-    size_t e = (size_t)max_source_elems(P) * nrhs * 2;
+    size_t e = (size_t)max_source_elems(P) * nrhs * 2 * (P->opt.tc_precision == 2 ? 2 : 1);
     W.ahi = (__half*)take(e * 2);
     W.alo = (__half*)take(e * 2);
     W.ascale = (float*)take((size_t)max_source_rows(P) * nrhs * 4);
@@ -1485,8 +1488,8 @@ void build_images(dfmm_plan_s* P, cudaStream_t s) {
     if (g->npairs == 0 || g->nops == 0 || !on_tensor_cores(P, *g)) continue;
     g->op_scale = P->ar.alloc<float>(g->nops);
     if (split_complex(P, *g)) {
-      g->img = P->ar.alloc<__half>(cx_image_elems(g->M, g->Kd, g->nops));
-      build_cx_image(g->ops, g->M, g->Kd, g->nops, g->img, g->op_scale, s);
+      g->img = (__half*)P->ar.alloc<unsigned char>(cx_image_bytes(g->M, g->Kd, g->nops, P->opt.tc_precision));
+      build_cx_image(g->ops, g->M, g->Kd, g->nops, g->img, g->op_scale, P->opt.tc_precision, s);
     } else {
       g->img = P->ar.alloc<__half>(tc_image_elems(g->M, g->Kd, g->nops));
       build_tc_image(g->ops, g->M, g->Kd, g->nops, g->img, g->op_scale, s);
@@ -1596,6 +1599,9 @@ int dfmm_plan(const double* points, int64_t N, double K, double eps, const dfmm_
     if (o.p2p_mode < 0 || o.p2p_mode > 2) return fail(DFMM_ERR_INVALID, "p2p_mode must be 0, 1 or 2");
     if (o.tc_layout < 0 || o.tc_layout > 1) return fail(DFMM_ERR_INVALID, "tc_layout must be 0 or 1");
     if (o.tc_accumulate < 0 || o.tc_accumulate > 1) return fail(DFMM_ERR_INVALID, "tc_accumulate must be 0 or 1");
+    if (o.tc_precision < 0 || o.tc_precision > 2) return fail(DFMM_ERR_INVALID, "tc_precision must be 0, 1 or 2");
+    if (o.tc_precision != 0 && o.tc_layout == 1)
+      return fail(DFMM_ERR_INVALID, "the BF16 and TF32 splits need the split-complex form (tc_layout 0)");
     // automatic near field: FP32 coordinates with exact close-pair
     // corrections for eps >= 1e-5, double-float coordinates below
     if (o.p2p_mode == 0) o.p2p_mode = eps >= 1e-5 ? 2 : 1;

@@ -13,8 +13,13 @@
 //  * One CTA computes a tile of 128 gathered columns (pairs x right-hand
 //    sides) against one operator, with tcgen05.mma kind::f16, M = 128,
 //    N = r_t <= 128, K = 16, FP32 accumulation in tensor memory.
-//  * Scaled FP16 split as in m2l_tc.cu: x / s = hi + lo per source row and
-//    T / t = hi + lo per operator; hi hi products go to the accumulators
+//  * Scaled split as in m2l_tc.cu: x / s = hi + lo per source row and
+//    T / t = hi + lo per operator, in one of three element types (KIND):
+//    FP16 (kind::f16, the default), BF16 (kind::f16 with BF16 operands:
+//    "3xBF16", about 16 bits) or TF32 (kind::tf32: "3xTF32", about 22 bits,
+//    half the FP16 rate).  Every tile is 64 bytes per row and K step 32
+//    bytes whatever the type, so one layout serves all three.  hi hi
+//    products go to the accumulators
 //    Re Y, Im Y and the cross terms hi lo + lo hi to a second pair re y, im y
 //    (tensor-core accumulation truncates), added in FP32 by the epilogue.
 //    4 accumulators x r_t <= 512 tensor-memory columns.  12 MMAs per K step.
@@ -27,6 +32,7 @@
 //    interleaved target components 2p .. 2p + 3: one 16-byte reduction
 //    (red.global.add.v4.f32), and one warp instruction covers 8 target rows x
 //    64 contiguous bytes.
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -41,26 +47,82 @@ namespace {
 using namespace tc;
 
 constexpr int CX_M = 128;                          // gathered columns per tile
-constexpr int CX_BK = 32;                          // K values (of one half) per stage
+constexpr int CX_SEG = 64;                         // bytes per row of a tile: one K chunk of one half
 constexpr int CX_NMAX = 128;                       // target rank
 constexpr int CX_PRODUCERS = 128;                  // warps 0-3: gather
 constexpr int CX_MMA_WARP = 8;                     // warps 4-7: epilogue; warp 8: MMA issuer
 constexpr int CX_THREADS = 288;
 constexpr int CX_STAGES = 3;
-constexpr int CX_A_TILE = CX_M * CX_BK * 2;        // 8 KB: one of xr hi, xr lo, xi hi, xi lo
-constexpr int CX_B_MAX = 4 * CX_NMAX * CX_BK * 2;  // 32 KB: Tr hi, Tr lo, Ti hi, Ti lo
+constexpr int CX_A_TILE = CX_M * CX_SEG;          // 8 KB: one of xr hi, xr lo, xi hi, xi lo
+constexpr int CX_B_MAX = 4 * CX_NMAX * CX_SEG;     // 32 KB: Tr hi, Tr lo, Ti hi, Ti lo
 constexpr int CX_STAGE = 4 * CX_A_TILE + CX_B_MAX;
 constexpr int CX_SMEM = CX_STAGES * CX_STAGE + 1024 + 256;
 constexpr int CX_TMEM_COLS = 512;
-constexpr uint32_t CX_SBO = (CX_BK / 8) * 128;     // 512 B between 8-row groups
+constexpr uint32_t CX_SBO = (CX_SEG / 16) * 128;   // 512 B between 8-row groups
 
-__host__ __device__ __forceinline__ uint32_t ckmaj(int row, int k) { return tc::kmaj_off(row, k, CX_SBO); }
+// byte offset of byte b (even) of row `row` of a tile in the stage layout
+__host__ __device__ __forceinline__ uint32_t ckmaj(int row, int b) { return tc::kmaj_off(row, b / 2, CX_SBO); }
+
+// element types: 0 = FP16, 1 = BF16, 2 = TF32 (stored as FP32 bit patterns)
+template <int KIND> struct Elem;
+template <> struct Elem<0> {
+  using T = __half;
+  static __device__ __forceinline__ void split(float v, T& h, T& l) {
+    h = __float2half_rn(v);
+    l = __float2half_rn(v - __half2float(h));
+  }
+};
+template <> struct Elem<1> {
+  using T = __nv_bfloat16;
+  static __device__ __forceinline__ void split(float v, T& h, T& l) {
+    h = __float2bfloat16_rn(v);
+    l = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+};
+__device__ __forceinline__ uint32_t to_tf32(float v) {   // round to the nearest TF32 (ties away)
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(v));
+  return r;
+}
+template <> struct Elem<2> {
+  using T = uint32_t;
+  static __device__ __forceinline__ void split(float v, T& h, T& l) {
+    h = to_tf32(v);
+    l = to_tf32(v - __uint_as_float(h));
+  }
+};
+template <int KIND> __host__ __device__ constexpr int elem_bytes() { return KIND == 2 ? 4 : 2; }
+template <int KIND> __host__ __device__ constexpr int seg_elems() { return CX_SEG / elem_bytes<KIND>(); }   // K values per chunk
+template <int KIND> __host__ __device__ constexpr int kstep_elems() { return 32 / elem_bytes<KIND>(); }    // K values per MMA
+
+// instruction descriptor: D f32, both operands K-major, M = 128, N = n; A and
+// B FP16 / BF16 (kind::f16) or TF32 (kind::tf32); neg_a negates A
+template <int KIND>
+__device__ __forceinline__ uint32_t idesc_cx(int n, bool neg_a) {
+  const uint32_t ty = KIND == 0 ? 0u : (KIND == 1 ? 1u : 2u);
+  return (1u << 4) | (ty << 7) | (ty << 10) | ((neg_a ? 1u : 0u) << 13) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(128 >> 4) << 24);
+}
+
+template <int KIND>
+__device__ __forceinline__ void mma_cx(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if (KIND == 2)
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  else
+    mma_f16(d_tmem, a, b, idesc, acc);
+}
 
 // Source rows (interleaved complex, len = 2 r floats) -> scaled FP16 hi / lo
 // rows with the real parts first and the imaginary parts second; one warp per
 // row, one power-of-two scale per row.
-__global__ void split_cx_kernel(const float* __restrict__ x, int64_t rows, int r, __half* __restrict__ hi,
-                                __half* __restrict__ lo, float* __restrict__ scale) {
+template <int KIND>
+__global__ void split_cx_kernel(const float* __restrict__ x, int64_t rows, int r, typename Elem<KIND>::T* __restrict__ hi,
+                                typename Elem<KIND>::T* __restrict__ lo, float* __restrict__ scale) {
+  using E = Elem<KIND>;
+  using T = typename E::T;
   const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (row >= rows) return;
@@ -76,49 +138,57 @@ __global__ void split_cx_kernel(const float* __restrict__ x, int64_t rows, int r
   const float s = pow2_above(m);
   const float inv = 1.f / s;
   if (lane == 0) scale[row] = s;
-  __half* h = hi + row * len;
-  __half* l = lo + row * len;
+  T* h = hi + row * len;
+  T* l = lo + row * len;
   for (int k = lane * 4; k < len; k += 128) {   // complex elements k/2 and k/2 + 1
     const float4 v = *(const float4*)(xr + k);
-    __half hr0, hi0, hr1, hi1, lr0, li0, lr1, li1;
-    split_h(v.x * inv, hr0, lr0);
-    split_h(v.y * inv, hi0, li0);
-    split_h(v.z * inv, hr1, lr1);
-    split_h(v.w * inv, hi1, li1);
+    T hr0, hi0, hr1, hi1, lr0, li0, lr1, li1;
+    E::split(v.x * inv, hr0, lr0);
+    E::split(v.y * inv, hi0, li0);
+    E::split(v.z * inv, hr1, lr1);
+    E::split(v.w * inv, hi1, li1);
     const int q = k >> 1;
-    *(__half2*)(h + q) = __halves2half2(hr0, hr1);
-    *(__half2*)(h + r + q) = __halves2half2(hi0, hi1);
-    *(__half2*)(l + q) = __halves2half2(lr0, lr1);
-    *(__half2*)(l + r + q) = __halves2half2(li0, li1);
+    h[q] = hr0;
+    h[q + 1] = hr1;
+    h[r + q] = hi0;
+    h[r + q + 1] = hi1;
+    l[q] = lr0;
+    l[q + 1] = lr1;
+    l[r + q] = li0;
+    l[r + q + 1] = li1;
   }
 }
 
 // Operator image: for every (operator, K chunk c) the four tiles Tr hi, Tr lo,
 // Ti hi, Ti lo of M rows x 32 fp16 values (row p, column q = 32 c + kk holds
 // T[p][q] / scale[op]), in the stage layout; zero beyond Kd.
+template <int KIND>
 __global__ void op_image_cx_kernel(const float2* __restrict__ ops, const float* __restrict__ scale, int M, int Kd,
-                                   int nops, __half* __restrict__ img) {
-  const int nchunk = (Kd + CX_BK - 1) / CX_BK;
+                                   int nops, unsigned char* __restrict__ img) {
+  using E = Elem<KIND>;
+  using T = typename E::T;
+  constexpr int BKE = seg_elems<KIND>(), EB = elem_bytes<KIND>();
+  const int nchunk = (Kd + BKE - 1) / BKE;
   const int64_t g = blockIdx.x;   // (op, c)
   const int c = (int)(g % nchunk);
   const int op = (int)(g / nchunk);
   if (op >= nops) return;
-  __half* base = img + g * (int64_t)(4 * M * CX_BK);
-  const float2* T = ops + (size_t)op * M * Kd;
+  unsigned char* base = img + g * (int64_t)(4 * M * CX_SEG);
+  const float2* Top = ops + (size_t)op * M * Kd;
   const float inv = 1.f / scale[op];
-  for (int e = threadIdx.x; e < M * CX_BK; e += blockDim.x) {
-    const int p = e / CX_BK, kk = e % CX_BK;
-    const int q = c * CX_BK + kk;
+  for (int e = threadIdx.x; e < M * BKE; e += blockDim.x) {
+    const int p = e / BKE, kk = e % BKE;
+    const int q = c * BKE + kk;
     float2 t = make_float2(0.f, 0.f);
-    if (q < Kd) t = T[(size_t)p * Kd + q];
-    __half rh, rl, ih, il;
-    split_h(t.x * inv, rh, rl);
-    split_h(t.y * inv, ih, il);
-    const uint32_t off = ckmaj(p, kk) / 2;
-    base[off] = rh;
-    base[M * CX_BK + off] = rl;
-    base[2 * M * CX_BK + off] = ih;
-    base[3 * M * CX_BK + off] = il;
+    if (q < Kd) t = Top[(size_t)p * Kd + q];
+    T rh, rl, ih, il;
+    E::split(t.x * inv, rh, rl);
+    E::split(t.y * inv, ih, il);
+    const uint32_t off = ckmaj(p, kk * EB);
+    *(T*)(base + off) = rh;
+    *(T*)(base + M * CX_SEG + off) = rl;
+    *(T*)(base + 2 * M * CX_SEG + off) = ih;
+    *(T*)(base + 3 * M * CX_SEG + off) = il;
   }
 }
 
@@ -143,8 +213,9 @@ __device__ __forceinline__ void named_bar_cx() { asm volatile("bar.sync 1, %0;" 
 // component (2 r_t columns) and two tensor-memory buffers, so that the MMAs
 // of a tile overlap the epilogue of the previous one; the cross terms then
 // accumulate with the truncation of the large terms.
-template <bool ONE>
+template <int KIND, bool ONE>
 __global__ __launch_bounds__(CX_THREADS, 1) void gemm_cx_kernel(GemmArgs a, TcArgs t, unsigned* status) {
+  constexpr int EB = elem_bytes<KIND>(), BKE = seg_elems<KIND>(), KSTEP = kstep_elems<KIND>();
   extern __shared__ unsigned char smem_raw[];
   __shared__ int s_start;
   __shared__ int s_flag[2];
@@ -158,10 +229,10 @@ __global__ __launch_bounds__(CX_THREADS, 1) void gemm_cx_kernel(GemmArgs a, TcAr
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int N = a.M;     // target rank: the MMA's N
   const int Kh = a.Kd;   // source rank: K of each half
-  const int nchunk = (Kh + CX_BK - 1) / CX_BK;
+  const int nchunk = (Kh + BKE - 1) / BKE;
   const int64_t nitems = a.ntiles;
-  const uint32_t b_bytes = (uint32_t)(4 * N * CX_BK * 2);
-  const int64_t op_elems = (int64_t)nchunk * 4 * N * CX_BK;
+  const uint32_t b_bytes = (uint32_t)(4 * N * CX_SEG);
+  const int64_t op_bytes = (int64_t)nchunk * 4 * N * CX_SEG;
 
   if (tid == 0) s_start = (*(volatile unsigned*)status & kStatusTimeout) ? 0 : 1;
   __syncthreads();
@@ -192,7 +263,8 @@ __global__ __launch_bounds__(CX_THREADS, 1) void gemm_cx_kernel(GemmArgs a, TcAr
   if (warp < CX_PRODUCERS / 32) {
     // ---------------- producers ----------------
     const int piece = tid & 3, seg = (tid >> 2) & 3, rg = tid >> 4;
-    const __half* sarr = ((seg & 1) ? t.src_lo : t.src_hi) + ((seg & 2) ? Kh : 0) + 8 * piece;
+    const unsigned char* sarr =
+        (const unsigned char*)((seg & 1) ? t.src_lo : t.src_hi) + ((seg & 2) ? Kh * EB : 0) + 16 * piece;
     int64_t g = 0;   // chunks issued by this CTA
     bool ok = true;
     // The source row of each gathered column: (pair, right-hand side) -> source
@@ -224,10 +296,10 @@ __global__ __launch_bounds__(CX_THREADS, 1) void gemm_cx_kernel(GemmArgs a, TcAr
       tile_n = tile_nn;
       load_rows(tile_n, rows_n);
       tile_nn = it + 2 * (int64_t)G < nitems ? a.tiles[it + 2 * G] : make_int4(0, 0, 0, 0);
-      const __half* srow[16];
+      const unsigned char* srow[16];
 #pragma unroll
-      for (int q = 0; q < 16; ++q) srow[q] = rows[q] >= 0 ? sarr + (int64_t)rows[q] * (2 * Kh) : nullptr;
-      const __half* img = t.img + tile.x * op_elems;
+      for (int q = 0; q < 16; ++q) srow[q] = rows[q] >= 0 ? sarr + (int64_t)rows[q] * (2 * Kh * EB) : nullptr;
+      const unsigned char* img = (const unsigned char*)t.img + tile.x * op_bytes;
       for (int c = 0; c < nchunk; ++c, ++g) {
         const int st = (int)(g % CX_STAGES);
         const int64_t j = g / CX_STAGES;
@@ -238,20 +310,20 @@ __global__ __launch_bounds__(CX_THREADS, 1) void gemm_cx_kernel(GemmArgs a, TcAr
           if (!ok) break;
         }
         const uint32_t sA = sbase + st * CX_STAGE + seg * CX_A_TILE;
-        const int k0 = c * CX_BK;
-        const bool kin = k0 + 8 * piece < Kh;
+        const int b0 = c * CX_SEG;   // byte offset of the chunk within a row half
+        const bool kin = b0 + 16 * piece < Kh * EB;
 #pragma unroll
         for (int q = 0; q < 16; ++q) {
-          const uint32_t dst = sA + ckmaj(rg + 8 * q, 8 * piece);
+          const uint32_t dst = sA + ckmaj(rg + 8 * q, 16 * piece);
           if (srow[q] && kin)
-            cp_async16(dst, srow[q] + k0);
+            cp_async16(dst, srow[q] + b0);
           else
             cp_async16_zero(dst, t.src_hi);
         }
         asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[st])) : "memory");
         if (tid == 0) {   // operator chunk: Tr hi, Tr lo, Ti hi, Ti lo
           mbar_expect_tx(smem_u32(&full[st]), b_bytes);
-          bulk_g2s(sbase + st * CX_STAGE + 4 * CX_A_TILE, img + (int64_t)c * 4 * N * CX_BK, b_bytes,
+          bulk_g2s(sbase + st * CX_STAGE + 4 * CX_A_TILE, img + (int64_t)c * 4 * N * CX_SEG, b_bytes,
                    smem_u32(&full[st]));
         }
       }
@@ -267,7 +339,7 @@ __global__ __launch_bounds__(CX_THREADS, 1) void gemm_cx_kernel(GemmArgs a, TcAr
       int i = 0;
       // wait_test: a wait that can only end by giving up; the CTA then takes the timeout path
       bool ok = !(a.wait_test && blockIdx.x == 0) || mbar_wait(smem_u32(never), 0u, status);
-      const uint32_t ip = idesc_f16(N), in = idesc_f16(N, true);
+      const uint32_t ip = idesc_cx<KIND>(N, false), in = idesc_cx<KIND>(N, true);
       for (int64_t it = blockIdx.x; it < nitems && ok; it += gridDim.x, ++i) {
         // buffer of this tile: ONE alternates two buffers of 2 r_t columns
         const int b = ONE ? (i & 1) : 0;
@@ -285,11 +357,11 @@ __global__ __launch_bounds__(CX_THREADS, 1) void gemm_cx_kernel(GemmArgs a, TcAr
           }
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // cp.async data -> async proxy
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const int ksteps = min(CX_BK, Kh - c * CX_BK) / 16;
+          const int ksteps = min(BKE, Kh - c * BKE) / KSTEP;
           const uint32_t xrh = sbase + st * CX_STAGE, xrl = xrh + CX_A_TILE, xih = xrl + CX_A_TILE,
                          xil = xih + CX_A_TILE;
-          const uint32_t trh = xil + CX_A_TILE, trl = trh + (uint32_t)(N * CX_BK * 2),
-                         tih = trl + (uint32_t)(N * CX_BK * 2), til = tih + (uint32_t)(N * CX_BK * 2);
+          const uint32_t trh = xil + CX_A_TILE, trl = trh + (uint32_t)(N * CX_SEG), tih = trl + (uint32_t)(N * CX_SEG),
+                         til = tih + (uint32_t)(N * CX_SEG);
           for (int s = 0; s < ksteps; ++s) {
             const uint32_t off = 256u * s;
             const uint32_t acc = (c > 0 || s > 0) ? 1u : 0u;
@@ -298,18 +370,18 @@ __global__ __launch_bounds__(CX_THREADS, 1) void gemm_cx_kernel(GemmArgs a, TcAr
             const uint64_t dtrh = smem_desc(trh + off, CX_SBO), dtrl = smem_desc(trl + off, CX_SBO),
                            dtih = smem_desc(tih + off, CX_SBO), dtil = smem_desc(til + off, CX_SBO);
             // Re y = Tr xr - Ti xi, Im y = Ti xr + Tr xi; hi hi terms into Y, the rest into y
-            mma_f16(YR, dxrh, dtrh, ip, acc);
-            mma_f16(YR, dxih, dtih, in, 1u);
-            mma_f16(YI, dxrh, dtih, ip, acc);
-            mma_f16(YI, dxih, dtrh, ip, 1u);
-            mma_f16(yr, dxrh, dtrl, ip, ONE ? 1u : acc);
-            mma_f16(yr, dxrl, dtrh, ip, 1u);
-            mma_f16(yr, dxih, dtil, in, 1u);
-            mma_f16(yr, dxil, dtih, in, 1u);
-            mma_f16(yi, dxrh, dtil, ip, ONE ? 1u : acc);
-            mma_f16(yi, dxrl, dtih, ip, 1u);
-            mma_f16(yi, dxih, dtrl, ip, 1u);
-            mma_f16(yi, dxil, dtrh, ip, 1u);
+            mma_cx<KIND>(YR, dxrh, dtrh, ip, acc);
+            mma_cx<KIND>(YR, dxih, dtih, in, 1u);
+            mma_cx<KIND>(YI, dxrh, dtih, ip, acc);
+            mma_cx<KIND>(YI, dxih, dtrh, ip, 1u);
+            mma_cx<KIND>(yr, dxrh, dtrl, ip, ONE ? 1u : acc);
+            mma_cx<KIND>(yr, dxrl, dtrh, ip, 1u);
+            mma_cx<KIND>(yr, dxih, dtil, in, 1u);
+            mma_cx<KIND>(yr, dxil, dtih, in, 1u);
+            mma_cx<KIND>(yi, dxrh, dtil, ip, ONE ? 1u : acc);
+            mma_cx<KIND>(yi, dxrl, dtih, ip, 1u);
+            mma_cx<KIND>(yi, dxih, dtrl, ip, 1u);
+            mma_cx<KIND>(yi, dxil, dtrh, ip, 1u);
           }
           mma_commit(smem_u32(&empty[st]));
           last = g;
@@ -407,29 +479,56 @@ int gemm_cx_columns() { return CX_M; }
 
 bool gemm_cx_supported(int M, int Kd) { return M % 16 == 0 && Kd % 16 == 0 && M >= 16 && M <= CX_NMAX; }
 
-int64_t cx_image_elems(int M, int Kd, int nops) {
-  const int nchunk = (Kd + CX_BK - 1) / CX_BK;
-  return (int64_t)nops * nchunk * 4 * M * CX_BK;
+int cx_elem_bytes(int kind) { return kind == 2 ? 4 : 2; }
+
+int64_t cx_image_bytes(int M, int Kd, int nops, int kind) {
+  const int bke = CX_SEG / cx_elem_bytes(kind);
+  const int nchunk = (Kd + bke - 1) / bke;
+  return (int64_t)nops * nchunk * 4 * M * CX_SEG;
 }
 
-void build_cx_image(const float2* ops, int M, int Kd, int nops, __half* img, float* scale, cudaStream_t s) {
+void build_cx_image(const float2* ops, int M, int Kd, int nops, void* img, float* scale, int kind, cudaStream_t s) {
   if (nops == 0) return;
   if (!gemm_cx_supported(M, Kd)) throw Error(-5, "split-complex stage needs ranks that are multiples of 16, <= 128");
   compute_op_scales(ops, (int64_t)M * Kd, nops, scale, s);
-  const int nchunk = (Kd + CX_BK - 1) / CX_BK;
-  op_image_cx_kernel<<<(unsigned)((int64_t)nops * nchunk), 256, 0, s>>>(ops, scale, M, Kd, nops, img);
+  const int bke = CX_SEG / cx_elem_bytes(kind);
+  const unsigned blocks = (unsigned)((int64_t)nops * ((Kd + bke - 1) / bke));
+  unsigned char* p = (unsigned char*)img;
+  if (kind == 0) op_image_cx_kernel<0><<<blocks, 256, 0, s>>>(ops, scale, M, Kd, nops, p);
+  else if (kind == 1) op_image_cx_kernel<1><<<blocks, 256, 0, s>>>(ops, scale, M, Kd, nops, p);
+  else op_image_cx_kernel<2><<<blocks, 256, 0, s>>>(ops, scale, M, Kd, nops, p);
   DFMM_CUDA(cudaGetLastError());
 }
 
-void launch_split_cx(const float2* x, int64_t rows, int r, __half* hi, __half* lo, float* scale, cudaStream_t s) {
+void launch_split_cx(const float2* x, int64_t rows, int r, void* hi, void* lo, float* scale, int kind, cudaStream_t s) {
   if (rows == 0) return;
   if (r % 16) throw Error(-5, "split-complex source rows need a rank that is a multiple of 16");
-  const int64_t threads = rows * 32;
-  split_cx_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>((const float*)x, rows, r, hi, lo, scale);
+  const unsigned grid = (unsigned)((rows * 32 + 255) / 256);
+  const float* xf = (const float*)x;
+  if (kind == 0)
+    split_cx_kernel<0><<<grid, 256, 0, s>>>(xf, rows, r, (__half*)hi, (__half*)lo, scale);
+  else if (kind == 1)
+    split_cx_kernel<1><<<grid, 256, 0, s>>>(xf, rows, r, (__nv_bfloat16*)hi, (__nv_bfloat16*)lo, scale);
+  else
+    split_cx_kernel<2><<<grid, 256, 0, s>>>(xf, rows, r, (uint32_t*)hi, (uint32_t*)lo, scale);
   DFMM_CUDA(cudaGetLastError());
 }
 
-void launch_gemm_stage_cx(const GemmArgs& a, const TcArgs& t, unsigned* status, bool one_acc, cudaStream_t s) {
+template <int KIND, bool ONE>
+void launch_cx(const GemmArgs& a, const TcArgs& t, unsigned* status, unsigned grid, cudaStream_t s) {
+  static bool attr[64] = {false};
+  int dev = 0;
+  DFMM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) throw Error(-1, "device ordinal out of range");
+  if (!attr[dev]) {
+    DFMM_CUDA(cudaFuncSetAttribute(gemm_cx_kernel<KIND, ONE>, cudaFuncAttributeMaxDynamicSharedMemorySize, CX_SMEM));
+    attr[dev] = true;
+  }
+  gemm_cx_kernel<KIND, ONE><<<grid, CX_THREADS, CX_SMEM, s>>>(a, t, status);
+}
+
+void launch_gemm_stage_cx(const GemmArgs& a, const TcArgs& t, unsigned* status, bool one_acc, int kind,
+                          cudaStream_t s) {
   if (a.ntiles == 0) return;
   if (!gemm_cx_supported(a.M, a.Kd) || a.src_ld != a.Kd)
     throw Error(-5, "split-complex stage needs ranks that are multiples of 16, <= 128, and dense source rows");
@@ -437,14 +536,18 @@ void launch_gemm_stage_cx(const GemmArgs& a, const TcArgs& t, unsigned* status, 
   int dev = 0;
   DFMM_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) throw Error(-1, "device ordinal out of range");
-  if (!nsm[dev]) {
-    DFMM_CUDA(cudaFuncSetAttribute(gemm_cx_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, CX_SMEM));
-    DFMM_CUDA(cudaFuncSetAttribute(gemm_cx_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, CX_SMEM));
-    DFMM_CUDA(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev));
-  }
+  if (!nsm[dev]) DFMM_CUDA(cudaDeviceGetAttribute(&nsm[dev], cudaDevAttrMultiProcessorCount, dev));
   const unsigned grid = (unsigned)std::min<int64_t>(a.ntiles, nsm[dev]);
-  if (one_acc) gemm_cx_kernel<true><<<grid, CX_THREADS, CX_SMEM, s>>>(a, t, status);
-  else gemm_cx_kernel<false><<<grid, CX_THREADS, CX_SMEM, s>>>(a, t, status);
+  if (kind == 0) {
+    if (one_acc) launch_cx<0, true>(a, t, status, grid, s);
+    else launch_cx<0, false>(a, t, status, grid, s);
+  } else if (kind == 1) {
+    if (one_acc) launch_cx<1, true>(a, t, status, grid, s);
+    else launch_cx<1, false>(a, t, status, grid, s);
+  } else {
+    if (one_acc) launch_cx<2, true>(a, t, status, grid, s);
+    else launch_cx<2, false>(a, t, status, grid, s);
+  }
   DFMM_CUDA(cudaGetLastError());
 }
 

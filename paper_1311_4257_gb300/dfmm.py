@@ -33,7 +33,7 @@ class Options(ctypes.Structure):
                 ("sketch_rows", ctypes.c_int32), ("eps_op_factor", ctypes.c_double), ("m2l_mode", ctypes.c_int32),
                 ("host_threads", ctypes.c_int32), ("cache_dir", ctypes.c_char_p), ("tc_stages", ctypes.c_int32),
                 ("wait_test", ctypes.c_int32), ("tile_order", ctypes.c_int32), ("p2p_mode", ctypes.c_int32),
-                ("tc_layout", ctypes.c_int32), ("tc_accumulate", ctypes.c_int32)]
+                ("tc_layout", ctypes.c_int32), ("tc_accumulate", ctypes.c_int32), ("tc_precision", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -166,7 +166,7 @@ class Plan:
                  sketch_rows: int = 0, eps_op_factor: float = 0.0, host_threads: int = 0,
                  cache_dir: str | None = None, m2l_mode: int = 0, tc_stages: int = 0, wait_test: int = 0,
                  tile_order: int = 0, p2p_mode: int = 0, tc_layout: int = 0,
-                 tc_accumulate: int = 0):
+                 tc_accumulate: int = 0, tc_precision: int = 0):
         import torch
         if not (isinstance(points, torch.Tensor) and points.is_cuda):
             points = torch.as_tensor(np.ascontiguousarray(points, dtype=np.float64), device="cuda")
@@ -177,7 +177,7 @@ class Plan:
         self.K = float(K)
         self.eps = float(eps)
         o = Options(leaf_max, sample_box, sample_far, sketch_rows, eps_op_factor, m2l_mode, host_threads,
-                    cache_dir.encode() if cache_dir else None, tc_stages, wait_test, tile_order, p2p_mode, tc_layout, tc_accumulate)
+                    cache_dir.encode() if cache_dir else None, tc_stages, wait_test, tile_order, p2p_mode, tc_layout, tc_accumulate, tc_precision)
         h = ctypes.c_void_p()
         _check(lib().dfmm_plan(points.data_ptr(), self.N, self.K, self.eps, ctypes.byref(o), ctypes.byref(h)))
         self._h = h

@@ -313,3 +313,23 @@ def test_split_complex_form_matches_real_block_form(nrhs):
     ud = OD.direct(p, f, t)
     for u in (u_cx, u_rb, u_one):
         assert OD.rel_err(u[:, t], ud) <= 1e-5
+
+
+def test_bf16_and_tf32_splits():
+    """The named splits of the precision form (configuration 3): 3xTF32 (TF32 hi / lo,
+    kind::tf32) and 3xBF16 (BF16 hi / lo) against the FP32 CUDA-core form and the direct
+    sum of Eq. 1.  TF32 carries 11 + 11 significant bits like the FP16 split and stays
+    within eps; BF16 carries 8 + 8 bits, so its error is bounded at the level its bits
+    allow, not at eps (the measured values are reported by bench.py --stage-errors)."""
+    p = workloads.sphere(8.0, 0)
+    f = workloads.densities(p.shape[0], 1, 17)
+    u_fp = _apply(_plan(p, 8.0, 1e-5, m2l_mode=1), f)
+    u_tf = _apply(_plan(p, 8.0, 1e-5, m2l_mode=2, tc_precision=2), f)
+    u_bf = _apply(_plan(p, 8.0, 1e-5, m2l_mode=2, tc_precision=1), f)
+    e_tf, e_bf = OD.rel_err(u_tf, u_fp), OD.rel_err(u_bf, u_fp)
+    assert 0 < e_tf < 2e-6
+    assert e_tf < e_bf < 2e-4          # 2^-16 per product, far above the 22-bit splits
+    t = np.arange(0, p.shape[0], 9)
+    ud = OD.direct(p, f, t)
+    assert OD.rel_err(u_tf[:, t], ud) <= 1e-5
+    assert OD.rel_err(u_bf[:, t], ud) <= 2e-4
