@@ -191,6 +191,43 @@ int64_t dfmm_plan_bytes(dfmm_plan_t plan);
 int dfmm_apply_batched(const dfmm_plan_t* plans, const void* const* f, void* const* u, const int* nrhs, int count,
                        cudaStream_t stream);
 
+/* The batched form with merged stages (the paper has no counterpart): the
+ * plans of a batch run wave by wave, one wave being the same step of every
+ * plan (by kind and box width), and the tensor-core translation stages of a
+ * wave (split-complex form) run as one persistent launch over a table of the
+ * plans' stages.  dfmm_batch_create fixes the device buffers f[k], u[k] (layout
+ * as in dfmm_apply, nrhs[k] right-hand sides, plans[k] of the current device),
+ * lays out one workspace per plan and the merged stage tables, and runs the
+ * batch once on `stream` (u = G f).  flags:
+ *   DFMM_BATCH_TUNE:  autotune: time every merged launch under each of three
+ *                     tile orders (by block of 8 MB or 2 MB of target rows, or
+ *                     by operator) and keep the fastest per launch;
+ *   DFMM_BATCH_GRAPH: capture one run of the batch into a CUDA graph.
+ * dfmm_batch_launch reruns the batch on `stream` (as one graph launch when
+ * captured) with the contents f has then; runs of one batch must not overlap
+ * (they share the workspaces).  Stages that the split-complex form does not
+ * take (target rank above 128, FP32 CUDA-core plans) run per plan.  Plans must
+ * stay alive while the batch exists.  dfmm_batch_destroy waits for the device
+ * and frees the batch. */
+typedef struct dfmm_batch_s* dfmm_batch_t;
+#define DFMM_BATCH_GRAPH 1
+#define DFMM_BATCH_TUNE 2
+typedef struct {
+  int64_t launches;            /* kernel launches of one run */
+  int64_t waves;               /* waves of the batch */
+  int64_t merged_launches;     /* merged translation launches of one run */
+  int64_t merged_stages;       /* plan stages they cover */
+  int32_t order_chosen[3];     /* merged launches per chosen tile order (8 MB, 2 MB blocks, operator) */
+  int32_t graph;               /* 1 if captured */
+  double tune_ms[3];           /* autotuning: summed merged-launch time under each order */
+} dfmm_batch_report;
+
+int dfmm_batch_create(const dfmm_plan_t* plans, const void* const* f, void* const* u, const int* nrhs, int count,
+                      cudaStream_t stream, int flags, dfmm_batch_t* out);
+int dfmm_batch_launch(dfmm_batch_t batch, cudaStream_t stream);
+int dfmm_batch_stats(dfmm_batch_t batch, dfmm_batch_report* out);
+int dfmm_batch_destroy(dfmm_batch_t batch);
+
 /* Export of the plan's tree and lists for parity tests (host buffers).
  * Call with a NULL buffer to get the required element count in *count.
  *   what = 0: Morton permutation, int64 [N]

@@ -17,6 +17,8 @@ struct ChkPt {
 
 // One translation stage: y[dst] += T_op x[src] for every (src, dst) pair,
 // columns = pairs x nrhs.  Operators complex64 [nops][M][Kd] row-major.
+struct CxStage;
+
 struct GemmArgs {
   const float2* ops;
   int M, Kd;
@@ -31,9 +33,26 @@ struct GemmArgs {
                             //    earlier in the apply, so results are stored, not added
   int wait_test;            // tensor-core form: 1 = CTA 0 waits on a barrier nothing arrives at
                             //    (exercises the bounded-wait failure path)
+  const CxStage* stages;    // split-complex form, several stages in one launch (device array), or
+                            //    nullptr: one stage given by the fields above and TcArgs
 };
 
 void launch_gemm_stage(const GemmArgs& a, cudaStream_t s);
+
+// One stage of a multi-stage split-complex launch (the batched form runs the
+// same step of several plans in one launch): its tiles carry the stage's index
+// in .w; all stages of a launch share M, Kd, dst_ld and the split's element type.
+struct CxStage {
+  const int2* pairs;        // (src row, dst row)
+  const void* src_hi;       // split source rows (launch_split_cx)
+  const void* src_lo;
+  const float* src_scale;
+  const void* img;          // operator image (build_cx_image)
+  const float* op_scale;
+  float2* dst;              // target states
+  int nrhs;
+  int store;
+};
 
 // Tensor-core form (tcgen05, scaled FP16 split) of the same stage; M and Kd
 // must be multiples of 8, source rows dense (src_ld == Kd); tiles hold up to

@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <deque>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -1151,13 +1152,15 @@ bool split_complex(const dfmm_plan_s* P, const GemmPlan& g) {
 }
 
 // tile_order: 0 = by the 64 MB rule above, 1 = always by target block, 2 = always by operator.
-std::vector<int4> make_tiles(const GemmPlan& g, int nrhs, int cols, int tile_order) {
+// block_bytes: target rows per block in the blocked order (8 MB unless the
+// batched form's autotuner tries another size).
+std::vector<int4> make_tiles(const GemmPlan& g, int nrhs, int cols, int tile_order, int64_t block_bytes = (int64_t)8 << 20) {
   const int per = std::max(1, cols / nrhs);
   std::vector<int4> t;
   std::vector<int64_t> key;
   const int64_t row_bytes = (int64_t)g.M * 8 * nrhs;
   const bool blocked = tile_order == 1 || (tile_order == 0 && (double)g.nops * g.M * g.Kd * 8.0 <= 64.0 * (1 << 20));
-  const int64_t block_rows = blocked ? std::max<int64_t>(1, ((int64_t)8 << 20) / std::max<int64_t>(1, row_bytes))
+  const int64_t block_rows = blocked ? std::max<int64_t>(1, block_bytes / std::max<int64_t>(1, row_bytes))
                                      : ((int64_t)1 << 40);
   for (const int4& grp : g.groups)
     for (int p = 0; p < grp.z; p += per) {
@@ -1186,16 +1189,57 @@ std::pair<int4*, int64_t> tiles_for(const dfmm_plan_s* P, Workspace* W, const Ge
   return W->tiles[key];
 }
 
+// A translation stage that the batched form runs in a merged launch.
+struct WaveGemm {
+  dfmm_plan_s* P;
+  Workspace* W;
+  const GemmPlan* g;
+  const float2* src;
+  int src_ld;
+  int64_t src_rows;
+  float2* dst;
+  int dst_ld;
+  int nrhs;
+  bool split;   // the stage's source buffer must be split first
+  int store;
+};
+
+// Wave filter of the batched form: run_apply acts only on the steps of one wave
+// (the same step, by kind and box width, in every plan), and hands its
+// split-complex translation stages to `collect` instead of launching them.
+struct WaveCtl {
+  int64_t wave;
+  std::vector<WaveGemm>* collect;
+  std::vector<int64_t>* keys;   // if set: the wave keys of the plan's steps are listed, nothing runs
+};
+
 struct Runner {
   dfmm_plan_s* P;
   Workspace* W;
   cudaStream_t s;
   int nrhs;
   int64_t* count;   // dry run: count launches only
+  WaveCtl* ctl = nullptr;
+  int64_t cur = 0;  // wave key of the next step
+
+  Runner& at(int64_t key) {
+    cur = key;
+    return *this;
+  }
+  // whether the current step is skipped by the wave filter (after listing its key)
+  bool skip() {
+    if (!ctl) return false;
+    if (ctl->keys) {
+      ctl->keys->push_back(cur);
+      return true;
+    }
+    return cur != ctl->wave;
+  }
 
   template <class Fn>
   void launch(int fam, double flops, double bytes, Fn&& fn) {
     if (count) { ++*count; return; }
+    if (skip()) return;
     ProfScope ps(W, s, fam, flops, bytes);
     fn();
   }
@@ -1216,6 +1260,12 @@ struct Runner {
     const bool split = tc && (key < 0 || key != split_key);
     if (tc) split_key = key;
     if (count) { count[0] += split ? 2 : 1; return; }
+    if (skip()) return;
+    if (ctl && ctl->collect && cx) {   // the batched form merges this stage with the other plans' same stage
+      ctl->collect->push_back(WaveGemm{P, W, &g, src, src_ld, src_rows, dst, dst_ld, nrhs, split,
+                                       (first && g.dst_unique) ? 1 : 0});
+      return;
+    }
     auto t = tiles_for(P, W, g, nrhs, tc ? gemm_tc_columns() : 64, s);
     GemmArgs a;
     a.ops = g.ops;
@@ -1231,6 +1281,7 @@ struct Runner {
     a.nrhs = nrhs;
     a.store = (first && g.dst_unique) ? 1 : 0;
     a.wait_test = P->opt.wait_test ? 1 : 0;
+    a.stages = nullptr;
     if (tc) {
       if (split) {
         ProfScope ps(W, s, F_SPLIT, 0.0, (double)src_rows * nrhs * src_ld * 16);
@@ -1250,15 +1301,33 @@ struct Runner {
 
 constexpr int kSrcS = 0, kSrcT = 64;   // source keys: outgoing / incoming states of a level
 
+// Wave keys of the steps of an apply: the same step (kind, box width) of
+// different plans gets the same key, and the keys of one plan's steps
+// increase in the order the apply runs them, so the batched form can run the
+// plans wave by wave.  lw = log2 of the box width.
+constexpr int64_t kWaveStart = 0;
+inline int64_t wave_p2m(int64_t lw) { return 1000 + (lw + 64) * 4; }
+inline int64_t wave_lf_m2m(int64_t lw) { return 1000 + (lw + 64) * 4 + 1; }
+constexpr int64_t kWaveTopV = 2000;
+inline int64_t wave_hf_m2m(int64_t lw) { return 3000 + (lw + 64) * 4; }
+inline int64_t wave_hf_m2l(int64_t lw) { return 3000 + (lw + 64) * 4 + 1; }
+inline int64_t wave_hf_l2l(int64_t lw) { return 4000 + (64 - lw) * 4; }
+inline int64_t wave_lf_down(int64_t lw, int k) { return 5000 + (64 - lw) * 8 + k; }
+inline int64_t wave_l2p(int64_t lw) { return 6000 + (64 - lw); }
+constexpr int64_t kWaveM2P = 6500, kWaveP2P = 7000, kWaveEnd = 8000;
+
 void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_t s, int64_t* count = nullptr,
-               Workspace* ext = nullptr) {
+               Workspace* ext = nullptr, WaveCtl* ctl = nullptr) {
   Workspace* W = count ? nullptr : (ext ? ext : get_workspace(P, s, nrhs));
   Runner R{P, W, s, nrhs, count};
+  R.ctl = ctl;
+  const int64_t lW = (int64_t)std::llround(std::log2(P->W));
+  auto lw = [&](int l) -> int64_t { return lW - l; };   // log2 of the width of level l
   const int64_t N = P->N;
   const int nl = P->nl;
   auto S = [&](int l) { return count ? (float2*)nullptr : W->S[l]; };
   auto T = [&](int l) { return count ? (float2*)nullptr : W->T[l]; };
-  const bool late = !count && !W->zero_late.empty();
+  const bool late = !count && !ctl && !W->zero_late.empty();
   if (late) {   // HF states: reset on a side stream while P2M and the V list run
     if (!W->side) {
       DFMM_CUDA(cudaStreamCreateWithFlags(&W->side, cudaStreamNonBlocking));
@@ -1270,16 +1339,18 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
     for (auto& z : W->zero_late) DFMM_CUDA(cudaMemsetAsync(z.first, 0, z.second, W->side));
     DFMM_CUDA(cudaEventRecord(W->join, W->side));
   }
-  if (!count) {
+  if (!count && !R.at(kWaveStart).skip()) {
     ProfScope ps(W, s, F_ZERO, 0.0, 0.0);
     for (auto& z : W->zero) DFMM_CUDA(cudaMemsetAsync(z.first, 0, z.second, s));
+    if (ctl)   // the batched form resets every state in line
+      for (auto& z : W->zero_late) DFMM_CUDA(cudaMemsetAsync(z.first, 0, z.second, s));
   }
-  R.launch(F_PERMUTE, 0.0, 20.0 * N * nrhs, [&] { launch_permute_in(f, P->perm, N, nrhs, W->fs, s); });
+  R.at(kWaveStart).launch(F_PERMUTE, 0.0, 20.0 * N * nrhs, [&] { launch_permute_in(f, P->perm, N, nrhs, W->fs, s); });
   // 1. LF upward: P2M at leaves, LF-M2M from the level below
   for (int l = nl - 1; l >= P->l_lf0; --l) {
     LFLevel& F = P->lf[l];
     if (F.n_l2p) {   // P2M: every leaf of this level, through its points' rows
-      R.launch(F_P2M_EVAL, 8.0 * F.r * F.npts * nrhs, F.npts * (8.0 * F.R + 8.0 * nrhs) + F.n_l2p * 8.0 * F.R * nrhs,
+      R.at(wave_p2m(lw(l))).launch(F_P2M_EVAL, 8.0 * F.r * F.npts * nrhs, F.npts * (8.0 * F.R + 8.0 * nrhs) + F.n_l2p * 8.0 * F.R * nrhs,
                [&] {
                  P2MRowsArgs a;
                  a.jobs = F.l2p_jobs;
@@ -1292,13 +1363,13 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
                  launch_p2m_rows(a, s);
                });
     }
-    if (l + 1 < nl) R.gemm(F.m2m, S(l + 1), P->lf[l + 1].R, P->lf[l + 1].nbox, S(l), F.R, kSrcS + l + 1);
+    if (l + 1 < nl) R.at(wave_lf_m2m(lw(l))).gemm(F.m2m, S(l + 1), P->lf[l + 1].R, P->lf[l + 1].nbox, S(l), F.R, kSrcS + l + 1);
   }
   // M2L of each level as soon as its outgoing states are complete, so that the
   // next M2M, which reads the same states, reuses their split.  The V list of the
   // top LF level: its L2L (from HF, summed over directions) adds anyway.
   if (P->l_lf0 < nl)
-    R.gemm(P->lf[P->l_lf0].v, S(P->l_lf0), P->lf[P->l_lf0].R, P->lf[P->l_lf0].nbox, T(P->l_lf0),
+    R.at(kWaveTopV).gemm(P->lf[P->l_lf0].v, S(P->l_lf0), P->lf[P->l_lf0].R, P->lf[P->l_lf0].nbox, T(P->l_lf0),
            P->lf[P->l_lf0].R, kSrcS + P->l_lf0);
   if (late) DFMM_CUDA(cudaStreamWaitEvent(s, W->join, 0));   // the HF states are reset
   // 2. HF upward: M2M, then that level's M2L
@@ -1307,13 +1378,13 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
       HFLevel& H = P->hf[l];
       int sld = (l == P->l1) ? P->lf[l + 1].R : P->hf[l + 1].R;
       int64_t srows = (l == P->l1) ? P->lf[l + 1].nbox : (int64_t)P->hf[l + 1].out_keys.size();
-      R.gemm(H.m2m, S(l + 1), sld, srows, S(l), H.R, kSrcS + l + 1);
-      R.gemm(H.m2l, S(l), H.R, (int64_t)H.out_keys.size(), T(l), H.R, kSrcS + l);
+      R.at(wave_hf_m2m(lw(l))).gemm(H.m2m, S(l + 1), sld, srows, S(l), H.R, kSrcS + l + 1);
+      R.at(wave_hf_m2l(lw(l))).gemm(H.m2l, S(l), H.R, (int64_t)H.out_keys.size(), T(l), H.R, kSrcS + l);
     }
     // 3. HF downward: L2L from the parent level
     for (int l = P->l_top + 1; l <= P->l1; ++l) {
       HFLevel& H = P->hf[l];
-      R.gemm(H.l2l, T(l - 1), P->hf[l - 1].R, (int64_t)P->hf[l - 1].in_keys.size(), T(l), H.R, kSrcT + l - 1);
+      R.at(wave_hf_l2l(lw(l))).gemm(H.l2l, T(l - 1), P->hf[l - 1].R, (int64_t)P->hf[l - 1].in_keys.size(), T(l), H.R, kSrcT + l - 1);
     }
   }
   // 4. LF downward
@@ -1321,14 +1392,15 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
     LFLevel& F = P->lf[l];
     if (l == P->l_lf0) {
       if (P->l_top >= 0)
-        R.gemm(F.l2l, T(P->l1), P->hf[P->l1].R, (int64_t)P->hf[P->l1].in_keys.size(), T(l), F.R, kSrcT + P->l1);
+        R.at(wave_lf_down(lw(l), 0)).gemm(F.l2l, T(P->l1), P->hf[P->l1].R, (int64_t)P->hf[P->l1].in_keys.size(), T(l), F.R, kSrcT + P->l1);
     } else {
-      R.gemm(F.l2l, T(l - 1), P->lf[l - 1].R, P->lf[l - 1].nbox, T(l), F.R, kSrcT + l - 1, true);
-      R.gemm(F.v, S(l), F.R, F.nbox, T(l), F.R, kSrcS + l);
+      R.at(wave_lf_down(lw(l), 0)).gemm(F.l2l, T(l - 1), P->lf[l - 1].R, P->lf[l - 1].nbox, T(l), F.R, kSrcT + l - 1,
+                                        true);
+      R.at(wave_lf_down(lw(l), 1)).gemm(F.v, S(l), F.R, F.nbox, T(l), F.R, kSrcS + l);
     }
     if (F.n_p2l) {
       double ev = (double)F.npts_x * 2 * F.r;
-      R.launch(F_P2L_EVAL, ev * (16 + 8.0 * nrhs), F.npts_x * (16.0 + 8.0 * nrhs) + F.n_p2l * 2.0 * F.R * 8 * nrhs, [&] {
+      R.at(wave_lf_down(lw(l), 2)).launch(F_P2L_EVAL, ev * (16 + 8.0 * nrhs), F.npts_x * (16.0 + 8.0 * nrhs) + F.n_p2l * 2.0 * F.R * 8 * nrhs, [&] {
         P2CArgs a;
         a.jobs = F.p2l_jobs;
         a.njobs = F.n_p2l;
@@ -1342,14 +1414,14 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
         a.nrhs = nrhs;
         launch_p2c(a, s);
       });
-      R.gemm(F.p2l, count ? nullptr : W->p2l, 2 * F.R, F.n_p2l, T(l), F.R, -1);
+      R.at(wave_lf_down(lw(l), 3)).gemm(F.p2l, count ? nullptr : W->p2l, 2 * F.R, F.n_p2l, T(l), F.R, -1);
     }
   }
   // 5. L2P at every leaf, M2P over the W list
   for (int l = P->l_lf0; l < nl; ++l) {
     LFLevel& F = P->lf[l];
     if (!F.n_l2p) continue;
-    R.launch(F_L2P, 8.0 * F.r * F.npts * nrhs, F.npts * (8.0 * F.R + 16.0 * nrhs) + F.n_l2p * 8.0 * F.R * nrhs, [&] {
+    R.at(wave_l2p(lw(l))).launch(F_L2P, 8.0 * F.r * F.npts * nrhs, F.npts * (8.0 * F.R + 16.0 * nrhs) + F.n_l2p * 8.0 * F.R * nrhs, [&] {
       L2PArgs a;
       a.map = F.l2p_map;
       a.nrows = F.n_l2p_rows;
@@ -1361,8 +1433,9 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
       launch_l2p(a, s);
     });
   }
-  for (auto& g : P->m2p) {
-    R.launch(F_M2P, 8.0 * P->lf[g.src_level].r * g.nrows * nrhs, g.nrows * (8.0 * g.R + 16.0 * nrhs), [&] {
+  for (size_t k = 0; k < P->m2p.size(); ++k) {
+    auto& g = P->m2p[k];
+    R.at(kWaveM2P + (int64_t)k).launch(F_M2P, 8.0 * P->lf[g.src_level].r * g.nrows * nrhs, g.nrows * (8.0 * g.R + 16.0 * nrhs), [&] {
       RowsArgs a;
       a.jobs = g.jobs;
       a.njobs = g.njobs;
@@ -1376,7 +1449,7 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
     });
   }
   // 6. near field
-  R.launch(F_P2P, (double)P->stats.p2p_interactions * (16.0 + 8.0 * nrhs), (double)N * (32.0 + 24.0 * nrhs), [&] {
+  R.at(kWaveP2P).launch(F_P2P, (double)P->stats.p2p_interactions * (16.0 + 8.0 * nrhs), (double)N * (32.0 + 24.0 * nrhs), [&] {
     P2PArgs a;
     a.leaf_range = P->p2p_range;
     a.nleaves = P->n_leaves;
@@ -1395,7 +1468,7 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
     if (P->opt.p2p_mode == 2) launch_p2p_fast(a, N, s);
     else launch_p2p(a, s);
   });
-  R.launch(F_PERMUTE, 0.0, 20.0 * N * nrhs, [&] { launch_permute_out(W->us, P->perm, N, nrhs, u, s); });
+  R.at(kWaveEnd).launch(F_PERMUTE, 0.0, 20.0 * N * nrhs, [&] { launch_permute_out(W->us, P->perm, N, nrhs, u, s); });
 }
 
 // Every translation stage of the plan, for laying out work tiles.
@@ -1562,6 +1635,191 @@ BatchStreams& batch_streams(int dev) {
     slot = std::move(B);
   }
   return *slot;
+}
+
+}  // namespace
+
+// The batched form with merged stages: the plans of a batch run wave by wave
+// (one wave = the same step of every plan, by kind and box width), and the
+// split-complex translation stages of a wave run as one launch over a table of
+// stages (tiles tagged with their stage).  Work tables and workspaces are laid
+// out once, for fixed device buffers f and u, so that a replay can be one
+// captured CUDA graph.
+struct dfmm_batch_s {
+  int device = 0;
+  std::vector<dfmm_plan_s*> plans;
+  std::vector<int> nrhs;
+  std::vector<const float2*> f;
+  std::vector<float2*> u;
+  DevArena ar;
+  std::vector<std::unique_ptr<Workspace>> ws;
+  std::vector<int64_t> waves;             // sorted union of the plans' wave keys
+  struct Merged {
+    int64_t wave = 0;
+    int M = 0, Kd = 0, kind = 0, one = 0;
+    std::vector<const GemmPlan*> key;     // its stages, in order
+    CxStage* stages = nullptr;
+    int4* tiles[3] = {nullptr, nullptr, nullptr};   // tile orders: blocked 8 MB, blocked 2 MB, by operator
+    int64_t ntiles[3] = {0, 0, 0};
+    int choice = 0;
+    double ms[3] = {0, 0, 0};
+  };
+  std::deque<Merged> merged;               // stable references while it grows
+  unsigned* status = nullptr;
+  int64_t launches = 0;                   // kernel launches of one run
+  int tuned = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  // the plans' per-point kernels of a wave run side by side on these streams
+  static constexpr int kSide = 8;
+  cudaStream_t side[kSide] = {};
+  cudaEvent_t fork = nullptr, join[kSide] = {};
+  ~dfmm_batch_s() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (int j = 0; j < kSide; ++j) {
+      if (side[j]) cudaStreamDestroy(side[j]);
+      if (join[j]) cudaEventDestroy(join[j]);
+    }
+    if (fork) cudaEventDestroy(fork);
+  }
+};
+
+namespace {
+
+constexpr int kBatchOrders = 3;
+
+void batch_tiles(const GemmPlan& g, int nrhs, int v, std::vector<int4>& out, int stage) {
+  std::vector<int4> t = v == 2 ? make_tiles(g, nrhs, gemm_cx_columns(), 2)
+                               : make_tiles(g, nrhs, gemm_cx_columns(), 1, (int64_t)(v == 0 ? 8 : 2) << 20);
+  for (int4 x : t) {
+    x.w = stage;
+    out.push_back(x);
+  }
+}
+
+dfmm_batch_s::Merged& merged_for(dfmm_batch_s* B, int64_t wave, int M, int Kd, int kind, int one,
+                                 const std::vector<WaveGemm>& list, cudaStream_t s) {
+  std::vector<const GemmPlan*> key;
+  for (auto& w : list) key.push_back(w.g);
+  for (auto& m : B->merged)
+    if (m.wave == wave && m.M == M && m.Kd == Kd && m.kind == kind && m.one == one && m.key == key) return m;
+  if (B->exec || B->tuned > 1) throw Error(DFMM_ERR_INVALID, "batch stage tables missing after set-up");
+  dfmm_batch_s::Merged m;
+  m.wave = wave;
+  m.M = M;
+  m.Kd = Kd;
+  m.kind = kind;
+  m.one = one;
+  m.key = key;
+  std::vector<CxStage> st;
+  std::vector<int4> tl[kBatchOrders];
+  for (size_t i = 0; i < list.size(); ++i) {
+    const WaveGemm& w = list[i];
+    CxStage c;
+    c.pairs = w.g->pairs;
+    c.src_hi = w.W->ahi;
+    c.src_lo = w.W->alo;
+    c.src_scale = w.W->ascale;
+    c.img = w.g->img;
+    c.op_scale = w.g->op_scale;
+    c.dst = w.dst;
+    c.nrhs = w.nrhs;
+    c.store = w.store;
+    st.push_back(c);
+    for (int v = 0; v < kBatchOrders; ++v) batch_tiles(*w.g, w.nrhs, v, tl[v], (int)i);
+  }
+  m.stages = B->ar.alloc<CxStage>((int64_t)st.size());
+  DFMM_CUDA(cudaMemcpyAsync(m.stages, st.data(), st.size() * sizeof(CxStage), cudaMemcpyHostToDevice, s));
+  for (int v = 0; v < kBatchOrders; ++v) {
+    m.ntiles[v] = (int64_t)tl[v].size();
+    m.tiles[v] = B->ar.alloc<int4>(std::max<int64_t>(1, m.ntiles[v]));
+    DFMM_CUDA(cudaMemcpyAsync(m.tiles[v], tl[v].data(), tl[v].size() * sizeof(int4), cudaMemcpyHostToDevice, s));
+  }
+  DFMM_CUDA(cudaStreamSynchronize(s));
+  B->merged.push_back(m);
+  return B->merged.back();
+}
+
+// One run of the batch on stream s.  force >= 0: every merged launch takes
+// tile order `force` and its time is recorded into ms[force] (autotuning).
+// Returns (stages merged, merged launches).
+std::pair<int64_t, int64_t> batch_run(dfmm_batch_s* B, cudaStream_t s, int force = -1) {
+  int64_t n_stages = 0, n_merged = 0;
+  std::vector<std::pair<dfmm_batch_s::Merged*, std::pair<cudaEvent_t, cudaEvent_t>>> timed;
+  int64_t launches = 0;
+  const int nside = (int)std::min<size_t>(dfmm_batch_s::kSide, B->plans.size());
+  for (int64_t wv : B->waves) {
+    std::vector<WaveGemm> coll;
+    // the plans' other steps of this wave (per-point kernels, stages outside the
+    // merged form) on the side streams, after everything queued on s
+    DFMM_CUDA(cudaEventRecord(B->fork, s));
+    for (int j = 0; j < nside; ++j) DFMM_CUDA(cudaStreamWaitEvent(B->side[j], B->fork, 0));
+    for (size_t k = 0; k < B->plans.size(); ++k) {
+      WaveCtl c{wv, &coll, nullptr};
+      run_apply(B->plans[k], B->f[k], B->u[k], B->nrhs[k], B->side[k % nside], nullptr, B->ws[k].get(), &c);
+    }
+    for (int j = 0; j < nside; ++j) {
+      DFMM_CUDA(cudaEventRecord(B->join[j], B->side[j]));
+      DFMM_CUDA(cudaStreamWaitEvent(s, B->join[j], 0));
+    }
+    // group the collected stages by launch shape, keeping the plans' order
+    std::vector<std::pair<std::array<int, 4>, std::vector<WaveGemm>>> groups;
+    for (auto& w : coll) {
+      std::array<int, 4> sh = {w.g->M, w.g->Kd, w.P->opt.tc_precision, w.P->opt.tc_accumulate};
+      auto it = std::find_if(groups.begin(), groups.end(), [&](const auto& g) { return g.first == sh; });
+      if (it == groups.end()) groups.push_back({sh, {w}});
+      else it->second.push_back(w);
+    }
+    for (auto& gr : groups) {
+      const auto& sh = gr.first;
+      auto& list = gr.second;
+      dfmm_batch_s::Merged& m = merged_for(B, wv, sh[0], sh[1], sh[2], sh[3], list, s);
+      for (auto& w : list)
+        if (w.split) {
+          launch_split_cx(w.src, w.src_rows * w.nrhs, w.src_ld, w.W->ahi, w.W->alo, w.W->ascale,
+                          w.P->opt.tc_precision, s);
+          ++launches;
+        }
+      const int v = force >= 0 ? force : m.choice;
+      GemmArgs a{};
+      a.M = m.M;
+      a.Kd = m.Kd;
+      a.tiles = m.tiles[v];
+      a.ntiles = m.ntiles[v];
+      a.src_ld = m.Kd;
+      a.dst_ld = m.M;
+      a.nrhs = 1;
+      a.stages = m.stages;
+      TcArgs t{};
+      cudaEvent_t e0 = nullptr, e1 = nullptr;
+      if (force >= 0) {
+        DFMM_CUDA(cudaEventCreate(&e0));
+        DFMM_CUDA(cudaEventCreate(&e1));
+        DFMM_CUDA(cudaEventRecord(e0, s));
+      }
+      launch_gemm_stage_cx(a, t, B->status, m.one == 1, m.kind, s);
+      ++launches;
+      ++n_merged;
+      n_stages += (int64_t)list.size();
+      if (force >= 0) {
+        DFMM_CUDA(cudaEventRecord(e1, s));
+        timed.push_back({&m, {e0, e1}});
+      }
+    }
+  }
+  if (force >= 0) {
+    DFMM_CUDA(cudaStreamSynchronize(s));
+    for (auto& t : timed) {
+      float ms = 0;
+      DFMM_CUDA(cudaEventElapsedTime(&ms, t.second.first, t.second.second));
+      t.first->ms[force] = ms;
+      cudaEventDestroy(t.second.first);
+      cudaEventDestroy(t.second.second);
+    }
+  }
+  (void)launches;
+  return {n_stages, n_merged};
 }
 
 }  // namespace
@@ -1785,6 +2043,127 @@ int dfmm_apply_batched(const dfmm_plan_t* plans, const void* const* f, void* con
     }
     return DFMM_OK;
   });
+}
+
+int dfmm_batch_create(const dfmm_plan_t* plans, const void* const* f, void* const* u, const int* nrhs, int count,
+                      cudaStream_t stream, int flags, dfmm_batch_t* out) {
+  return guarded([&]() -> int {
+    if (!out) return fail(DFMM_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (count < 1) return fail(DFMM_ERR_INVALID, "count must be >= 1");
+    if (!plans || !f || !u || !nrhs) return fail(DFMM_ERR_INVALID, "null argument");
+    if (flags & ~(DFMM_BATCH_GRAPH | DFMM_BATCH_TUNE)) return fail(DFMM_ERR_INVALID, "unknown batch flag");
+    int dev = -1;
+    DFMM_CUDA(cudaGetDevice(&dev));
+    std::unique_ptr<dfmm_batch_s> B(new dfmm_batch_s());
+    B->device = dev;
+    for (int k = 0; k < count; ++k) {
+      if (!plans[k] || !f[k] || !u[k]) return fail(DFMM_ERR_INVALID, "null plan or buffer in the batch");
+      if (nrhs[k] < 1 || nrhs[k] > 64) return fail(DFMM_ERR_INVALID, "nrhs must be in [1, 64]");
+      if (f[k] == u[k]) return fail(DFMM_ERR_INVALID, "f and u must not alias");
+      if (plans[k]->device != dev) return fail(DFMM_ERR_INVALID, "a plan of the batch belongs to another device");
+      if (plans[k]->opt.wait_test) return fail(DFMM_ERR_UNSUPPORTED, "wait_test plans cannot be batched");
+      B->plans.push_back(plans[k]);
+      B->nrhs.push_back(nrhs[k]);
+      B->f.push_back((const float2*)f[k]);
+      B->u.push_back((float2*)u[k]);
+    }
+    // one carved workspace per plan (work tables copied in here, before any capture)
+    for (int k = 0; k < count; ++k) {
+      std::unique_ptr<Workspace> W(new Workspace());
+      const size_t bytes = (size_t)workspace_bytes(B->plans[k], B->nrhs[k]);
+      char* base = B->ar.alloc<char>((int64_t)bytes);
+      carve_workspace(B->plans[k], B->nrhs[k], base, bytes, stream, *W);
+      B->ws.push_back(std::move(W));
+    }
+    B->status = B->ar.alloc<unsigned>(1);
+    DFMM_CUDA(cudaMemsetAsync(B->status, 0, 4, stream));
+    for (int j = 0; j < dfmm_batch_s::kSide; ++j) {
+      DFMM_CUDA(cudaStreamCreateWithFlags(&B->side[j], cudaStreamNonBlocking));
+      DFMM_CUDA(cudaEventCreateWithFlags(&B->join[j], cudaEventDisableTiming));
+    }
+    DFMM_CUDA(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
+    // the waves: the union of the plans' wave keys
+    for (int k = 0; k < count; ++k) {
+      std::vector<int64_t> keys;
+      WaveCtl c{0, nullptr, &keys};
+      run_apply(B->plans[k], B->f[k], B->u[k], B->nrhs[k], stream, nullptr, B->ws[k].get(), &c);
+      B->waves.insert(B->waves.end(), keys.begin(), keys.end());
+    }
+    std::sort(B->waves.begin(), B->waves.end());
+    B->waves.erase(std::unique(B->waves.begin(), B->waves.end()), B->waves.end());
+    // first run: lays out the merged stage tables; then the autotuner times each
+    // tile order per merged launch and keeps the fastest
+    auto nm = batch_run(B.get(), stream);
+    if (flags & DFMM_BATCH_TUNE) {
+      for (int v = 0; v < kBatchOrders; ++v) batch_run(B.get(), stream, v);
+      for (auto& m : B->merged) {
+        int best = 0;
+        for (int v = 1; v < kBatchOrders; ++v)
+          if (m.ms[v] < m.ms[best]) best = v;
+        m.choice = best;
+      }
+      batch_run(B.get(), stream);   // the result of the chosen orders
+    }
+    B->tuned = 2;
+    int64_t total = 0;
+    for (int k = 0; k < count; ++k) {
+      int64_t c = 0;
+      run_apply(B->plans[k], nullptr, nullptr, B->nrhs[k], nullptr, &c);
+      total += c;
+    }
+    B->launches = total - nm.first + nm.second;
+    DFMM_CUDA(cudaStreamSynchronize(stream));
+    if (flags & DFMM_BATCH_GRAPH) {
+      cudaStream_t cs;
+      DFMM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+      struct SG { cudaStream_t s; ~SG() { cudaStreamDestroy(s); } } sg{cs};
+      DFMM_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+      try {
+        batch_run(B.get(), cs);
+      } catch (...) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(cs, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+      }
+      DFMM_CUDA(cudaStreamEndCapture(cs, &B->graph));
+      DFMM_CUDA(cudaGraphInstantiate(&B->exec, B->graph, 0));
+    }
+    *out = B.release();
+    return DFMM_OK;
+  });
+}
+
+int dfmm_batch_launch(dfmm_batch_t batch, cudaStream_t stream) {
+  return guarded([&]() -> int {
+    if (!batch) return fail(DFMM_ERR_INVALID, "null batch");
+    if (batch->exec) DFMM_CUDA(cudaGraphLaunch(batch->exec, stream));
+    else batch_run(batch, stream);
+    return DFMM_OK;
+  });
+}
+
+int dfmm_batch_stats(dfmm_batch_t batch, dfmm_batch_report* out) {
+  if (!batch || !out) return fail(DFMM_ERR_INVALID, "null argument");
+  std::memset(out, 0, sizeof(*out));
+  out->launches = batch->launches;
+  out->waves = (int64_t)batch->waves.size();
+  out->merged_launches = (int64_t)batch->merged.size();
+  for (auto& m : batch->merged) {
+    out->merged_stages += (int64_t)m.key.size();
+    out->order_chosen[m.choice] += 1;
+    for (int v = 0; v < kBatchOrders; ++v) out->tune_ms[v] += m.ms[v];
+  }
+  out->graph = batch->exec ? 1 : 0;
+  return DFMM_OK;
+}
+
+int dfmm_batch_destroy(dfmm_batch_t batch) {
+  if (!batch) return DFMM_OK;
+  cudaDeviceSynchronize();
+  delete batch;
+  return DFMM_OK;
 }
 
 int dfmm_export(dfmm_plan_t plan, int what, void* buffer, int64_t* count) {

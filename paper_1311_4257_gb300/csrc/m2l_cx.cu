@@ -192,6 +192,23 @@ __global__ void op_image_cx_kernel(const float2* __restrict__ ops, const float* 
   }
 }
 
+// The stage of a tile: from the launch's stage table (tile .w), or the single
+// stage of GemmArgs / TcArgs.
+__device__ __forceinline__ CxStage stage_of(const GemmArgs& a, const TcArgs& t, int w) {
+  if (a.stages) return a.stages[w];
+  CxStage s;
+  s.pairs = a.pairs;
+  s.src_hi = t.src_hi;
+  s.src_lo = t.src_lo;
+  s.src_scale = t.src_scale;
+  s.img = t.img;
+  s.op_scale = t.op_scale;
+  s.dst = a.dst;
+  s.nrhs = a.nrhs;
+  s.store = a.store;
+  return s;
+}
+
 __device__ __forceinline__ void named_bar_cx() { asm volatile("bar.sync 1, %0;" ::"n"(CX_PRODUCERS) : "memory"); }
 
 // Persistent, warp-specialised stage kernel; CTA x takes tiles x, x + gridDim.x, ...
@@ -263,8 +280,6 @@ __global__ __launch_bounds__(CX_THREADS, 1) void gemm_cx_kernel(GemmArgs a, TcAr
   if (warp < CX_PRODUCERS / 32) {
     // ---------------- producers ----------------
     const int piece = tid & 3, seg = (tid >> 2) & 3, rg = tid >> 4;
-    const unsigned char* sarr =
-        (const unsigned char*)((seg & 1) ? t.src_lo : t.src_hi) + ((seg & 2) ? Kh * EB : 0) + 16 * piece;
     int64_t g = 0;   // chunks issued by this CTA
     bool ok = true;
     // The source row of each gathered column: (pair, right-hand side) -> source
@@ -272,34 +287,39 @@ __global__ __launch_bounds__(CX_THREADS, 1) void gemm_cx_kernel(GemmArgs a, TcAr
     // while this tile's chunks are issued, so their latency stays off the
     // gather's critical path.
     const int G = gridDim.x;
-    auto load_rows = [&](const int4& tl, int* srcrow) {
+    // per tile: this thread's source segment base and its 16 source rows
+    auto load_rows = [&](const int4& tl, int* srcrow, const unsigned char*& sbase_arr, const unsigned char*& img_tile) {
+      const CxStage sg = stage_of(a, t, tl.w);
+      sbase_arr = (const unsigned char*)((seg & 1) ? sg.src_lo : sg.src_hi) + ((seg & 2) ? Kh * EB : 0) + 16 * piece;
+      img_tile = (const unsigned char*)sg.img + tl.x * op_bytes;
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
         const int row = rg + 8 * q;
         srcrow[q] = -1;
-        if (row < tl.z * a.nrhs) {
-          if (a.nrhs == 1) srcrow[q] = a.pairs[tl.y + row].x;
-          else srcrow[q] = a.pairs[tl.y + row / a.nrhs].x * a.nrhs + row % a.nrhs;
+        if (row < tl.z * sg.nrhs) {
+          if (sg.nrhs == 1) srcrow[q] = sg.pairs[tl.y + row].x;
+          else srcrow[q] = sg.pairs[tl.y + row / sg.nrhs].x * sg.nrhs + row % sg.nrhs;
         }
       }
     };
     int4 tile_n = blockIdx.x < nitems ? a.tiles[blockIdx.x] : make_int4(0, 0, 0, 0);
     int rows_n[16];
-    load_rows(tile_n, rows_n);
+    const unsigned char *sarr_n = nullptr, *img_n = nullptr;
+    if (blockIdx.x < nitems) load_rows(tile_n, rows_n, sarr_n, img_n);
     int4 tile_nn = blockIdx.x + G < nitems ? a.tiles[blockIdx.x + G] : make_int4(0, 0, 0, 0);
     for (int64_t it = blockIdx.x; it < nitems && ok; it += G) {
-      const int4 tile = tile_n;
       int rows[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) rows[q] = rows_n[q];
+      const unsigned char* sarr = sarr_n;
+      const unsigned char* img = img_n;
       // prefetch: rows of the next tile, record of the one after
       tile_n = tile_nn;
-      load_rows(tile_n, rows_n);
+      if (it + G < nitems) load_rows(tile_n, rows_n, sarr_n, img_n);
       tile_nn = it + 2 * (int64_t)G < nitems ? a.tiles[it + 2 * G] : make_int4(0, 0, 0, 0);
       const unsigned char* srow[16];
 #pragma unroll
       for (int q = 0; q < 16; ++q) srow[q] = rows[q] >= 0 ? sarr + (int64_t)rows[q] * (2 * Kh * EB) : nullptr;
-      const unsigned char* img = (const unsigned char*)t.img + tile.x * op_bytes;
       for (int c = 0; c < nchunk; ++c, ++g) {
         const int st = (int)(g % CX_STAGES);
         const int64_t j = g / CX_STAGES;
@@ -318,7 +338,7 @@ __global__ __launch_bounds__(CX_THREADS, 1) void gemm_cx_kernel(GemmArgs a, TcAr
           if (srow[q] && kin)
             cp_async16(dst, srow[q] + b0);
           else
-            cp_async16_zero(dst, t.src_hi);
+            cp_async16_zero(dst, sarr);
         }
         asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[st])) : "memory");
         if (tid == 0) {   // operator chunk: Tr hi, Tr lo, Ti hi, Ti lo
@@ -399,6 +419,7 @@ __global__ __launch_bounds__(CX_THREADS, 1) void gemm_cx_kernel(GemmArgs a, TcAr
     int i = 0;
     for (int64_t it = blockIdx.x; it < nitems; it += gridDim.x, ++i) {
       const int4 tile = a.tiles[it];
+      const CxStage sg = stage_of(a, t, tile.w);
       float* out[4];
       float cs[4];
 #pragma unroll
@@ -406,11 +427,11 @@ __global__ __launch_bounds__(CX_THREADS, 1) void gemm_cx_kernel(GemmArgs a, TcAr
         const int col = 32 * quarter + 16 * (h >> 1) + (lane >> 2) + 8 * (h & 1);
         out[h] = nullptr;
         cs[h] = 0.f;
-        if (col < tile.z * a.nrhs) {
-          const int2 pr = a.pairs[tile.y + col / a.nrhs];
-          const int k = col % a.nrhs;
-          cs[h] = t.src_scale[(int64_t)pr.x * a.nrhs + k] * t.op_scale[tile.x];
-          out[h] = (float*)(a.dst + ((int64_t)pr.y * a.nrhs + k) * a.dst_ld) + 4 * (lane & 3);
+        if (col < tile.z * sg.nrhs) {
+          const int2 pr = sg.pairs[tile.y + col / sg.nrhs];
+          const int k = col % sg.nrhs;
+          cs[h] = sg.src_scale[(int64_t)pr.x * sg.nrhs + k] * sg.op_scale[tile.x];
+          out[h] = (float*)(sg.dst + ((int64_t)pr.y * sg.nrhs + k) * a.dst_ld) + 4 * (lane & 3);
         }
       }
       const int b = ONE ? (i & 1) : 0;
@@ -453,7 +474,7 @@ __global__ __launch_bounds__(CX_THREADS, 1) void gemm_cx_kernel(GemmArgs a, TcAr
                 const float re1 = (__uint_as_float(vr[r + 1]) + __uint_as_float(wr[r + 1])) * cc;
                 const float im1 = (__uint_as_float(vi[r + 1]) + __uint_as_float(wi[r + 1])) * cc;
                 if (o) {
-                  if (a.store) *(float4*)(o + f) = make_float4(re0, im0, re1, im1);
+                  if (sg.store) *(float4*)(o + f) = make_float4(re0, im0, re1, im1);
                   else red_add4(o + f, re0, im0, re1, im1);
                 }
               }

@@ -70,6 +70,12 @@ class KernelTime(ctypes.Structure):
                 ("flops", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
+class BatchReport(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("waves", ctypes.c_int64), ("merged_launches", ctypes.c_int64),
+                ("merged_stages", ctypes.c_int64), ("order_chosen", ctypes.c_int32 * 3), ("graph", ctypes.c_int32),
+                ("tune_ms", ctypes.c_double * 3)]
+
+
 class Peaks(ctypes.Structure):
     _fields_ = [("sm_count", ctypes.c_int32), ("reserved", ctypes.c_int32), ("fp32_fma_tflops", ctypes.c_double),
                 ("fp64_fma_tflops", ctypes.c_double), ("sincos_gops", ctypes.c_double),
@@ -113,6 +119,11 @@ def lib() -> ctypes.CDLL:
         L.dfmm_graph_create.argtypes = [vp, vp, vp, i32, vp, ctypes.POINTER(vp)]
         L.dfmm_graph_launch.argtypes = [vp, vp]
         L.dfmm_graph_destroy.argtypes = [vp]
+        L.dfmm_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                        ctypes.POINTER(i32), i32, vp, i32, ctypes.POINTER(vp)]
+        L.dfmm_batch_launch.argtypes = [vp, vp]
+        L.dfmm_batch_stats.argtypes = [vp, ctypes.POINTER(BatchReport)]
+        L.dfmm_batch_destroy.argtypes = [vp]
         L.dfmm_solve.argtypes = [vp, dbl, dbl, dbl, dbl, vp, vp, i32, i32, dbl, vp, ctypes.POINTER(i32),
                                  ctypes.POINTER(dbl)]
         L.dfmm_measure_peaks.argtypes = [ctypes.POINTER(Peaks)]
@@ -121,7 +132,8 @@ def lib() -> ctypes.CDLL:
                   "dfmm_plan_stats", "dfmm_export", "dfmm_representation", "dfmm_profile", "dfmm_apply_batched",
                   "dfmm_server_create", "dfmm_server_submit", "dfmm_server_wait", "dfmm_server_stats",
                   "dfmm_server_destroy", "dfmm_solve", "dfmm_graph_create", "dfmm_graph_launch",
-                  "dfmm_graph_destroy", "dfmm_measure_peaks"):
+                  "dfmm_graph_destroy", "dfmm_measure_peaks", "dfmm_batch_create", "dfmm_batch_launch",
+                  "dfmm_batch_stats", "dfmm_batch_destroy"):
             getattr(L, f).restype = i32
         _lib = L
     return _lib
@@ -330,6 +342,56 @@ def apply_batched(plans, fs, us=None, stream=None):
     R = (ctypes.c_int * n)(*[int(f.shape[0]) for f in fs])
     _check(lib().dfmm_apply_batched(P, F, U, R, n, _stream_ptr(stream)))
     return us
+
+
+BATCH_GRAPH, BATCH_TUNE = 1, 2
+
+
+class Batch:
+    """dfmm_batch_*: the batched form with one merged launch per translation stage
+    across the plans, on fixed device buffers (fs[k] read, us[k] written).
+    launch() recomputes every u[k] = G_k f[k] from the current contents of f."""
+
+    def __init__(self, plans, fs, us=None, stream=None, graph: bool = True, tune: bool = True):
+        import torch
+        n = len(plans)
+        fs = [f.reshape(1, -1) if f.ndim == 1 else f for f in fs]
+        for p, f in zip(plans, fs):
+            if f.dtype != torch.complex64 or not f.is_cuda or not f.is_contiguous() or f.shape[1] != p.N:
+                raise TypeError("each f must be a contiguous cuda complex64 [nrhs, N] tensor of its plan")
+        self.plans, self.fs = list(plans), fs
+        self.us = us if us is not None else [torch.empty_like(f) for f in fs]
+        vp = ctypes.c_void_p
+        P = (vp * n)(*[p._h.value for p in plans])
+        F = (vp * n)(*[f.data_ptr() for f in fs])
+        U = (vp * n)(*[u.data_ptr() for u in self.us])
+        R = (ctypes.c_int * n)(*[int(f.shape[0]) for f in fs])
+        h = ctypes.c_void_p()
+        flags = (BATCH_GRAPH if graph else 0) | (BATCH_TUNE if tune else 0)
+        _check(lib().dfmm_batch_create(P, F, U, R, n, _stream_ptr(stream), flags, ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(lib().dfmm_batch_launch(self._h, _stream_ptr(stream)))
+        return self.us
+
+    def stats(self) -> dict:
+        r = BatchReport()
+        _check(lib().dfmm_batch_stats(self._h, ctypes.byref(r)))
+        return {"launches": r.launches, "waves": r.waves, "merged_launches": r.merged_launches,
+                "merged_stages": r.merged_stages, "order_chosen": list(r.order_chosen), "graph": r.graph,
+                "tune_ms": list(r.tune_ms)}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().dfmm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

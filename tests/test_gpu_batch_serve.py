@@ -60,6 +60,36 @@ def test_apply_batched_equals_single_applies(plans):
     assert _rel(us[2].cpu().numpy()[:, t], ud) < 1e-5
 
 
+def test_merged_batch_equals_single_applies(plans):
+    """The batched form with one merged launch per translation stage across the
+    plans (dfmm_batch_*), autotuned and captured as a graph: each geometry's
+    result equals its single apply, after set-up and on replays with new
+    densities; fewer launches than the plans' applies together."""
+    import torch
+    from paper_1311_4257_gb300 import Batch
+    nrhs = [1, 4, 2, 3]
+    fs = [torch.as_tensor(workloads.densities(p.N, r, 70 + k).astype(np.complex64), device="cuda")
+          for k, ((p, _), r) in enumerate(zip(plans, nrhs))]
+    b = Batch([p for p, _ in plans], fs, graph=True, tune=True)
+    torch.cuda.synchronize()
+    st = b.stats()
+    assert st["graph"] == 1 and st["merged_launches"] > 0 and st["merged_stages"] > st["merged_launches"]
+    assert sum(st["order_chosen"]) == st["merged_launches"]
+    assert st["launches"] < sum(p.launches(r) for (p, _), r in zip(plans, nrhs))
+    for rnd in range(3):
+        if rnd:
+            for k, f in enumerate(fs):   # new densities in the same buffers, then one replay
+                f.copy_(torch.as_tensor(workloads.densities(f.shape[1], f.shape[0], 80 + 10 * rnd + k)
+                                        .astype(np.complex64), device="cuda"))
+            b.launch()
+            torch.cuda.synchronize()
+        for (p, _), f, u in zip(plans, fs, b.us):
+            ref = p.apply(f)
+            torch.cuda.synchronize()
+            assert _rel(u.cpu().numpy(), ref.cpu().numpy()) < 1e-6
+    b.close()
+
+
 def test_apply_batched_rejects_bad_arguments(plans):
     import torch
     from paper_1311_4257_gb300 import DfmmError, apply_batched
