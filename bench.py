@@ -531,6 +531,7 @@ def run_batch12(args):
     dev = max(OD.rel_err(a.cpu().numpy().astype(np.complex128), b.cpu().numpy().astype(np.complex128))
               for a, b in zip(us2, us))
     merged = {"ms_per_step": ms_m, "points_rhs_per_s": work / (ms_m / 1e3), "setup_seconds": setup_s,
+              "launches_of_the_single_applies": int(sum(pl.launches(r) for pl, (_, _, _, r) in zip(plans, geo))),
               "max_rel_diff_vs_stream_form": dev, **batch.stats()}
     batch.close()
     plain = _plain_rate([(p, K, 1e-5, r) for _, p, K, r in geo], args.cache_dir) if args.compare else None
