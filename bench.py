@@ -30,6 +30,8 @@ METRIC = "FMM matvec points*RHS/s at <=1e-5 rel err, chosen vs plain; p50/p99 la
 WORKLOADS = {
     "sphere_K64": dict(K=64.0, seed=1, eps=1e-5, desc="sphere diameter 64, N=1,286,796 (seed 1), eps 1e-5"),
     "sphere_K8": dict(K=8.0, seed=0, eps=1e-6, desc="sphere diameter 8, N=20,106 (seed 0), eps 1e-6"),
+    "sphere_K8_eps1e8": dict(K=8.0, seed=0, eps=1e-8,
+                             desc="sphere diameter 8, N=20,106 (seed 0), eps 1e-8 (FP64 form, complex128)"),
     "sphere_K16": dict(K=16.0, seed=1, eps=1e-5, desc="sphere diameter 16, N=80,424 (seed 1), eps 1e-5"),
     "sphere_K32": dict(K=32.0, seed=1, eps=1e-5, desc="sphere diameter 32, N=321,699 (seed 1), eps 1e-5"),
     "ellipsoid_K128": dict(K=128.0, seed=2, eps=1e-5, axes=(64.0, 32.0, 16.0),
@@ -212,7 +214,7 @@ def run_ours(args, wl):
     plan = Plan(p, K, wl["eps"], cache_dir=args.cache_dir, m2l_mode={"auto": 0, "fp32": 1, "tc": 2}[args.form])
     plan_s = time.perf_counter() - t0
     st = plan.stats()
-    fd = torch.as_tensor(f.astype(np.complex64), device="cuda")
+    fd = torch.as_tensor(f.astype(plan.np_dtype), device="cuda")
     ud = torch.empty_like(fd)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
@@ -261,7 +263,7 @@ def run_ours(args, wl):
         graph_ms = e0.elapsed_time(e1) / args.steps
         gr.close()
     # end to end through the host-buffer entry point (pinned buffers)
-    fh = torch.as_tensor(f.astype(np.complex64)).pin_memory()
+    fh = torch.as_tensor(f.astype(plan.np_dtype)).pin_memory()
     uh = torch.empty_like(fh).pin_memory()
     plan.apply_host_ptr(fh.data_ptr(), uh.data_ptr(), nrhs)
     torch.cuda.synchronize()
@@ -283,6 +285,11 @@ def run_ours(args, wl):
     else:
         pk["fp32_source"] = "derived: 152 SM x 128 lanes x 2 x max SM clock"
     tc = (args.form == "tc") or (args.form == "auto" and wl["eps"] >= 1e-5)
+    fp64 = plan.arith == 64   # FP64 form (eps < 1e-6): CUDA-core FP64 arithmetic throughout
+    if fp64:
+        pk["fp32_tflops"] = probes["fp64_fma_tflops"] if probes else 1.25
+        pk["fp32_source"] = ("measured (dfmm_measure_peaks, FP64 FMA probe)" if probes else
+                             "GB300 nominal FP64 rate 1.25 TFLOP/s (the probe measures 1.25)")
     # roofline of each stage family: translations on the tensor pipe (useful flops
     # against the FP16 peak / 3 MMAs) or the FP32 pipe, P2P on the FP32 pipe,
     # row streams and permutes on HBM
@@ -298,10 +305,10 @@ def run_ours(args, wl):
         if name in gemm_fams and "tflops" in entry:
             pkv = pk["bf16_tflops"] / 3 if tc else pk["fp32_tflops"]
             entry["frac"] = entry["tflops"] / pkv
-            entry["bound"] = "tensor (FP16 peak / 3)" if tc else "fp32 FMA"
+            entry["bound"] = "tensor (FP16 peak / 3)" if tc else ("fp64 FMA" if fp64 else "fp32 FMA")
         elif name in ("p2p", "p2l_eval") and "tflops" in entry:
             entry["frac"] = entry["tflops"] / pk["fp32_tflops"]
-            entry["bound"] = "fp32 FMA (16 + 8 nrhs flops per interaction)"
+            entry["bound"] = ("fp64" if fp64 else "fp32") + " FMA (16 + 8 nrhs flops per interaction)"
         elif "gbs" in entry:
             entry["frac"] = entry["gbs"] / pk["hbm_gbs"]
             entry["bound"] = "hbm"
@@ -324,28 +331,32 @@ def run_ours(args, wl):
                     "peak_source": "measured bf16 dense %.1f TF/s (FP16 runs at the same rate), / 3 MMAs per "
                                    "useful product" % pk["bf16_tflops"]}
     else:
-        roofline = {"kernel": "gemm_stage_kernel (all translation stages)", "bound": "alu", "achieved": achieved,
+        roofline = {"kernel": "gemm64_kernel (all translation stages)" if fp64 else
+                    "gemm_stage_kernel (all translation stages)", "bound": "alu", "achieved": achieved,
                     "peak": pk["fp32_tflops"], "unit": "TFLOP/s", "frac": achieved / pk["fp32_tflops"],
-                    "peak_source": "FP32 CUDA-core peak, %s" % pk["fp32_source"]}
+                    "peak_source": "%s CUDA-core peak, %s" % ("FP64" if fp64 else "FP32", pk["fp32_source"])}
     roofline.update({"traffic": traffic_for("gemm_cx_kernel", "m2l_cx.cu+dfmm.cpp", args.workload) if tc else
-                     traffic_for("gemm_stage_kernel", "apply.cu+dfmm.cpp", args.workload),
+                     (None if fp64 else traffic_for("gemm_stage_kernel", "apply.cu+dfmm.cpp", args.workload)),
                      "launches_per_step": launches / nprof, "ms_per_launch": g_ms / launches,
                      "flops_per_launch": g_flops / launches, "share_of_step": share})
     out = {"metric": METRIC, "value": value, "unit": "points*RHS/s", "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "c64 (fp32)", "data": "synthetic",
+           "vs_baseline": None, "dtype": "c128 (fp64)" if fp64 else "c64 (fp32)", "data": "synthetic",
            "config": {"workload": wl["desc"], "N": N, "K": K, "eps": wl["eps"], "nrhs": nrhs,
-                      "form": "tensor cores (tcgen05, scaled FP16 hi/lo split)" if tc else "FP32 CUDA cores",
+                      "form": "tensor cores (tcgen05, scaled FP16 hi/lo split)" if tc else
+                      ("FP64 CUDA cores" if fp64 else "FP32 CUDA cores"),
                       "parallelism": "replicas" if world > 1 else "1 gpu",
                       "l2": "inputs larger than L2 (plan %.1f GB resident, states re-zeroed each step)" % (st["plan_bytes"] / 1e9),
-                      "plan_seconds": plan_s},
+                      "plan_seconds": plan_s,
+                      "plan_phase_seconds": dict(zip(("tree_lists", "skeletons", "rep_upload", "operators", "rows",
+                                                      "near_field", "tc_images"), st["plan_phase_seconds"]))},
            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
            "graph_ms_per_step": graph_ms,
-           "e2e": {"value": N * nrhs / (e2e_ms / 1e3), "unit": "points*RHS/s", "h2d_bytes_per_step": 8 * N * nrhs,
-                   "d2h_bytes_per_step": 8 * N * nrhs},
+           "e2e": {"value": N * nrhs / (e2e_ms / 1e3), "unit": "points*RHS/s",
+                   "h2d_bytes_per_step": fd.element_size() * N * nrhs, "d2h_bytes_per_step": fd.element_size() * N * nrhs},
            "gpu_launches": plan.launches(nrhs) * args.steps,
            "clocks": clocks, "roofline": roofline, "stages": stages, "probes": probes}
-    if args.compare and rank == 0:
+    if args.compare and rank == 0 and not fp64:
         # the plain form (FP32 CUDA cores, one RHS) and the batched chosen form (16 RHS)
         plain = Plan(p, K, wl["eps"], cache_dir=args.cache_dir, m2l_mode=1)
         for _ in range(2):

@@ -57,8 +57,9 @@ typedef struct {
   int32_t leaf_max;        /* [64] an LF box with more points is split (Sec. 2.2) */
   int32_t sample_box;      /* [1024] box samples per skeleton */
   int32_t sample_far;      /* [4096] far-region samples per skeleton */
-  int32_t sketch_rows;     /* [400] rows of the random sketch in the pivoted QR */
-  double eps_op_factor;    /* [0.3] skeleton tolerance = eps * factor */
+  int32_t sketch_rows;     /* [0 = 400 if eps >= 1e-7, else 800] rows of the random sketch in the
+                              pivoted QR (at least twice the largest rank) */
+  double eps_op_factor;    /* [0 = 0.3 if eps >= 1e-7, else 0.1] skeleton tolerance = eps * factor */
   int32_t m2l_mode;        /* [0] translations on: 0 = automatic (tensor cores if eps >= 1e-5, else
                               FP32 CUDA cores), 1 = FP32 CUDA cores, 2 = tensor cores (tcgen05,
                               scaled FP16 hi/lo split; adds about 2e-6 relative error) */
@@ -100,6 +101,13 @@ typedef struct {
                               "3xBF16"); 2 = TF32 (11 + 11 bits with an 8-bit exponent, kind::tf32
                               at half the FP16 rate, "3xTF32").  1 and 2 need tc_layout 0; stages
                               whose target rank exceeds 128 then run on the FP32 CUDA cores. */
+  int32_t arith;           /* [0] arithmetic of the apply: 0 = automatic (32 if eps >= 1e-6, else
+                              64); 32 = the FP32 forms above (complex64 f and u); 64 = FP64
+                              throughout (translations, rows, check points and near field on
+                              the CUDA cores; operators kept in complex128), for eps down to
+                              1e-8.  With 64, f and u of every apply entry point are complex128
+                              [nrhs][N], m2l_mode 2 is refused and the other m2l / p2p / tc
+                              options are ignored; dfmm_solve takes arith 32 plans only. */
 } dfmm_options;
 
 /* Build a plan (Sec. 2.2 octree, lists, Eq. 2 representations and the
@@ -118,8 +126,9 @@ int dfmm_plan(const double* points, int64_t N, double K, double eps,
               const dfmm_options* opts, dfmm_plan_t* out);
 
 /* The matvec u = G f (Alg. 1 passes plus the near field).
- *   f      : device pointer, complex64 [nrhs][N] in the caller's point order.
- *   u      : device pointer, complex64 [nrhs][N]; overwritten, never
+ *   f      : device pointer, complex64 [nrhs][N] in the caller's point order
+ *            (complex128 for a plan whose arith is 64: eps < 1e-6 by default).
+ *   u      : device pointer, complex64 [nrhs][N] (complex128 likewise); overwritten, never
  *            accumulated.  Must not alias f.
  *   nrhs   : number of right-hand sides, 1 <= nrhs <= 64.
  *   stream : CUDA stream; the call only enqueues work (no host sync).
@@ -163,6 +172,14 @@ typedef struct {
   double other_translation_flops; /* M2M, L2L, LF-M2L, P2M/L2P GEMMs per RHS */
   int64_t hf_ops[32];          /* distinct HF-M2L operators per level (offsets up to cube symmetry) */
   int64_t p2p_close_pairs;     /* FP32 near field: pairs with a stored exact correction */
+  int32_t arith;               /* 32 or 64: arithmetic of the apply (options.arith resolved) */
+  int32_t reserved;
+  double plan_phase_seconds[8];   /* wall time of dfmm_plan by phase: 0 = points, sort, octree, lists
+                                     and active directions; 1 = skeletons (Eq. 2 representations,
+                                     host, from the disk cache when present); 2 = their upload;
+                                     3 = translation operators (M2M, M2L, L2L, P2L projections);
+                                     4 = per-point rows (L2P, P2M, M2P); 5 = near-field lists and
+                                     close pairs; 6 = tensor-core operator images; 7 = unused */
 } dfmm_stats;
 
 int dfmm_plan_stats(dfmm_plan_t plan, dfmm_stats* out);
@@ -257,7 +274,7 @@ int dfmm_export(dfmm_plan_t plan, int what, void* buffer, int64_t* count);
  * dfmm_noalloc_capacity() bytes (64 MiB), which every device that loads the
  * library holds until the process exits.
  *   plan, f, u, nrhs, stream : as for dfmm_apply (device pointers, complex64
- *            [nrhs][N], u overwritten).  The plan must belong to the current
+ *            [nrhs][N], complex128 for an arith 64 plan; u overwritten).  The plan must belong to the current
  *            device.
  * An apply fits exactly when dfmm_apply_workspace_bytes(plan, nrhs) <=
  * dfmm_noalloc_capacity(); otherwise the call returns DFMM_ERR_UNSUPPORTED,
@@ -301,7 +318,8 @@ int dfmm_graph_destroy(dfmm_graph_t graph);
  * return *iters (if not NULL) holds the number of matvecs of the Krylov
  * iterations, and *relres (if not NULL) the true relative residual of x
  * (one more matvec).  The accuracy of A is that of the plan (eps), so tol
- * below about eps is not meaningful.  Allocates (restart + 2) N complex64 of
+ * below about eps is not meaningful.  The plan must compute in FP32 (arith
+ * 32; else DFMM_ERR_UNSUPPORTED).  Allocates (restart + 2) N complex64 of
  * device workspace per call; synchronises `stream` at every iteration (the
  * small least-squares problem is solved on the host).  Returns DFMM_OK
  * whether or not tol was reached (compare *relres), or an error status. */
@@ -319,13 +337,13 @@ int dfmm_solve(dfmm_plan_t plan, double alpha_re, double alpha_im, double beta_r
  * request on the same plan, up to max_rhs right-hand sides in total, into one
  * apply whose right-hand sides sit side by side.  A group starts when a
  * stream is free and its footprint fits in the arena: 2 N nrhs complex64
- * staging plus dfmm_apply_workspace_bytes.  Requests that arrive while others
+ * (complex128 for an arith 64 plan) staging plus dfmm_apply_workspace_bytes.  Requests that arrive while others
  * run are admitted as streams and memory free up.  A request that could never
  * fit fails with DFMM_ERR_OOM.
  *
  * dfmm_server_submit queues one request: nrhs right-hand sides of the plan's
  * N points, host buffers f_host (read) and u_host (written) of nrhs * N
- * complex64 each, laid out as in dfmm_apply (pinned memory makes the copies
+ * complex64 each (complex128 for an arith 64 plan), laid out as in dfmm_apply (pinned memory makes the copies
  * asynchronous).  The caller keeps both buffers alive and untouched until
  * dfmm_server_wait has returned for the ticket written to *ticket.
  * dfmm_server_wait blocks until the request has finished or timeout_seconds

@@ -111,6 +111,8 @@ struct P2CArgs {
   const float2* fs;          // [N][nrhs]
   float2* out;               // [rows][nrhs][ld]
   int nrhs;
+  const double* chk64;       // FP64 form: the check points, [nchk][3]
+  const float4* pts_lo;      // FP64 form: low parts of the local coordinates
 };
 void launch_p2c(const P2CArgs& a, cudaStream_t s);
 
@@ -183,5 +185,18 @@ void launch_p2p_fast(const P2PArgs& a, int64_t npoints, cudaStream_t s);
 // distance 0.  Pass 2: fills j and w at the CSR offsets off[N + 1].
 void launch_p2p_close(const P2PArgs& a, float delta, int32_t* cnt, unsigned* degenerate, const int32_t* off,
                       int32_t* close_j, float2* close_w, cudaStream_t s);
+
+// FP64 forms (apply64.cu), for eps < 1e-6: the same argument structs, with
+// every complex array (operators, rows, states, densities, potentials)
+// holding complex128 (double2) elements at the same indices.  Representation
+// ranks up to 512; the check-point form needs P2CArgs.chk64 and .pts_lo.
+void launch_gemm_stage64(const GemmArgs& a, cudaStream_t s);
+void launch_permute_in64(const float2* f, const int32_t* perm, int64_t N, int nrhs, float2* fs, cudaStream_t s);
+void launch_permute_out64(const float2* us, const int32_t* perm, int64_t N, int nrhs, float2* u, cudaStream_t s);
+void launch_p2c64(const P2CArgs& a, cudaStream_t s);
+void launch_rows64(const RowsArgs& a, cudaStream_t s);
+void launch_l2p64(const L2PArgs& a, cudaStream_t s);
+void launch_p2m_rows64(const P2MRowsArgs& a, cudaStream_t s);
+void launch_p2p64(const P2PArgs& a, cudaStream_t s);
 
 }  // namespace dfmm

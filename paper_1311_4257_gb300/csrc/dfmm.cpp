@@ -91,6 +91,7 @@ struct LFLevel {
   int64_t nbox = 0;
   GemmPlan m2m, l2l, v, p2l;   // m2m from l+1, l2l from l-1 (LF or HF)
   ChkPt* chk_b2 = nullptr;
+  double* chk64 = nullptr;         // FP64 form: the check points b2, [2r][3]
   int4* p2l_jobs = nullptr;
   float4* p2l_shifts = nullptr;
   int64_t n_p2l = 0;
@@ -175,6 +176,8 @@ struct dfmm_plan_s {
   int64_t N = 0;
   double K = 0, W = 0, eps = 0, eps_op = 0;
   dfmm_options opt{};
+  bool fp64 = false;   // FP64 form (options.arith 64): complex128 densities, states and operators
+  int cw = 1;          // complex element width in float2 units (2 in the FP64 form)
   DevArena ar;
   TreeBuilder tree;
   int32_t* perm = nullptr;
@@ -357,17 +360,21 @@ T* upload(const std::vector<T>& v, DevArena& ar, cudaStream_t s) {
   return d;
 }
 
-// conjugate transpose of a 2r x r matrix, columns scaled, padded to R x 2R, complex64
-float2* upload_projection(const std::vector<cd>& Q, int r, const double* colscale, int R, DevArena& ar,
+// conjugate transpose of a 2r x r matrix, columns scaled, padded to R x 2R:
+// complex64, or complex128 for the FP64 form
+float2* upload_projection(const std::vector<cd>& Q, int r, const double* colscale, int R, bool fp64, DevArena& ar,
                           cudaStream_t s) {
-  std::vector<float2> h((size_t)R * 2 * R, make_float2(0, 0));
+  std::vector<double2> h((size_t)R * 2 * R, make_double2(0, 0));
   for (int i = 0; i < r; ++i)
     for (int j = 0; j < 2 * r; ++j) {
       cd v = std::conj(Q[(size_t)j * r + i]);
       if (colscale) v *= colscale[j];
-      h[(size_t)i * 2 * R + j] = make_float2((float)v.real(), (float)v.imag());
+      h[(size_t)i * 2 * R + j] = make_double2(v.real(), v.imag());
     }
-  return upload(h, ar, s);
+  if (fp64) return (float2*)upload(h, ar, s);
+  std::vector<float2> f(h.size());
+  for (size_t i = 0; i < h.size(); ++i) f[i] = make_float2((float)h[i].x, (float)h[i].y);
+  return upload(f, ar, s);
 }
 
 ChkPt* upload_chk(const std::vector<double>& pts, int n, DevArena& ar, cudaStream_t s) {
@@ -512,6 +519,10 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
       P->stats.slots_in[l] = (int64_t)H.in_keys.size();
     }
   }
+  double* ph = P->stats.plan_phase_seconds;
+  double tp = t0;
+  auto phase = [&](int k) { const double t = now(); ph[k] += t - tp; tp = t; };
+  phase(0);
   // ---- representations (host skeletons, built in parallel)
   double w_top = has_hf ? LV[P->l_top].w : 1.0;
   SkelParams sp;
@@ -534,6 +545,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
     for (int c : level_cells[l]) need.push_back({LV[l].w, c});
   }
   P->reps->prepare(need);
+  phase(1);
   std::vector<DevRep> dreps;
   std::map<std::pair<int, int>, int> ridx;   // (level, cell) -> dreps index
   for (int l = (has_hf ? P->l_top : P->l_lf0); l < nl; ++l) {
@@ -542,7 +554,9 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
     // ranks padded to 8; to 16 for the split-complex tensor-core form (the MMA's N and K steps)
     const int pad = (P->opt.m2l_mode == 2 && P->opt.tc_layout != 1) ? 16 : 8;
     int R = round_up(std::max(rmax, pad), pad);
-    if (R > 256) throw Error(DFMM_ERR_UNSUPPORTED, "representation rank above 256");
+    // the FP32 row kernels take ranks up to 256, the FP64 form's up to 512
+    if (R > (P->fp64 ? 512 : 256))
+      throw Error(DFMM_ERR_UNSUPPORTED, P->fp64 ? "representation rank above 512" : "representation rank above 256");
     if (l <= P->l1) P->hf[l].R = R;
     else { P->lf[l].R = R; P->lf[l].r = rmax; }
     P->stats.rank[l] = R;
@@ -561,6 +575,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
   auto center = [&](int l, int64_t b, int d) { return -0.5 * P->W + (LV[l].h_coords[3 * b + d] + 0.5) * LV[l].w; };
   P->zero_shift = upload(std::vector<float4>{make_float4(0, 0, 0, 0)}, ar, s);
 
+  phase(2);
   // ---- LF levels
   for (int l = P->l_lf0; l < nl; ++l) {
     LFLevel& F = P->lf[l];
@@ -570,8 +585,9 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
     const Rep& rp = P->reps->get(F.w, -1);
     const int R = F.R;
     F.chk_b2 = upload_chk(rp.b2, 2 * rp.r, ar, s);
+    if (P->fp64) F.chk64 = upload(rp.b2, ar, s);
     F.p2l.M = R; F.p2l.Kd = 2 * R; F.p2l.nops = 1;
-    F.p2l.ops = upload_projection(rp.Qi, rp.r, nullptr, R, ar, s);
+    F.p2l.ops = upload_projection(rp.Qi, rp.r, nullptr, R, P->fp64, ar, s);
     std::vector<int4> jobs;
     std::vector<int32_t> op;
     std::vector<int2> pr;
@@ -626,8 +642,8 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
       }
       F.v.M = R; F.v.Kd = R; F.v.nops = (int)specs.size();
       if (!specs.empty()) {
-        F.v.ops = ar.alloc<float2>((size_t)specs.size() * R * R);
-        form_ops(kOpM2L, specs, dreps, R, R, F.v.ops, cb, ar, s);
+        F.v.ops = ar.alloc<float2>(((size_t)specs.size() * R * R) * P->cw);
+        form_ops(kOpM2L, specs, dreps, R, R, F.v.ops, P->fp64, cb, ar, s);
       }
       F.v.fam = F_M2L_LF;
       F.v.flops_rhs = 8.0 * rp.r * rp.r * V.n;
@@ -649,8 +665,8 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
       int Rc = P->lf[l + 1].R;
       (void)C;
       F.m2m.M = R; F.m2m.Kd = Rc; F.m2m.nops = 8;
-      F.m2m.ops = ar.alloc<float2>((size_t)8 * R * Rc);
-      form_ops(kOpM2M, specs, dreps, R, Rc, F.m2m.ops, cb, ar, s);
+      F.m2m.ops = ar.alloc<float2>(((size_t)8 * R * Rc) * P->cw);
+      form_ops(kOpM2M, specs, dreps, R, Rc, F.m2m.ops, P->fp64, cb, ar, s);
       op.clear(); pr.clear();
       for (int64_t c = 0; c < Lc.n; ++c) {
         op.push_back(octant_of(&Lc.h_coords[3 * c]));
@@ -673,8 +689,8 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
         for (int d = 0; d < 3; ++d) specs[o].shift[d] = dl[d];
       }
       F.l2l.M = R; F.l2l.Kd = Rp; F.l2l.nops = 8;
-      F.l2l.ops = ar.alloc<float2>((size_t)8 * R * Rp);
-      form_ops(kOpL2L, specs, dreps, R, Rp, F.l2l.ops, cb, ar, s);
+      F.l2l.ops = ar.alloc<float2>(((size_t)8 * R * Rp) * P->cw);
+      form_ops(kOpL2L, specs, dreps, R, Rp, F.l2l.ops, P->fp64, cb, ar, s);
       op.clear(); pr.clear();
       for (int64_t c = 0; c < LV[l].n; ++c) {
         op.push_back(octant_of(&LV[l].h_coords[3 * c]));
@@ -745,8 +761,8 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
         P->stats.hf_ops[l] = (int64_t)specs.size();
         H.m2l.M = R; H.m2l.Kd = R; H.m2l.nops = (int)specs.size();
         if (!specs.empty()) {
-          H.m2l.ops = ar.alloc<float2>((size_t)specs.size() * R * R);
-          form_ops(kOpM2L, specs, dreps, R, R, H.m2l.ops, cb, ar, s);
+          H.m2l.ops = ar.alloc<float2>(((size_t)specs.size() * R * R) * P->cw);
+          form_ops(kOpM2L, specs, dreps, R, R, H.m2l.ops, P->fp64, cb, ar, s);
         }
         finish_gemm(H.m2l, op, pr, ar, s);
       }
@@ -769,8 +785,8 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
             specs.push_back(sp2);
           }
         H.m2m.M = R; H.m2m.Kd = Rc; H.m2m.nops = (int)specs.size();
-        H.m2m.ops = ar.alloc<float2>(std::max<size_t>(1, specs.size()) * R * Rc);
-        form_ops(kOpM2M, specs, dreps, R, Rc, H.m2m.ops, cb, ar, s);
+        H.m2m.ops = ar.alloc<float2>((std::max<size_t>(1, specs.size()) * R * Rc) * P->cw);
+        form_ops(kOpM2M, specs, dreps, R, Rc, H.m2m.ops, P->fp64, cb, ar, s);
         op.clear(); pr.clear();
         for (size_t k = 0; k < H.out_keys.size(); ++k) {
           int b = H.out_keys[k] / H.nd, d = H.out_keys[k] % H.nd;
@@ -809,8 +825,8 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
             specs.push_back(sp2);
           }
         H.l2l.M = R; H.l2l.Kd = Hp.R; H.l2l.nops = (int)specs.size();
-        H.l2l.ops = ar.alloc<float2>(std::max<size_t>(1, specs.size()) * R * Hp.R);
-        form_ops(kOpL2L, specs, dreps, R, Hp.R, H.l2l.ops, cb, ar, s);
+        H.l2l.ops = ar.alloc<float2>((std::max<size_t>(1, specs.size()) * R * Hp.R) * P->cw);
+        form_ops(kOpL2L, specs, dreps, R, Hp.R, H.l2l.ops, P->fp64, cb, ar, s);
         op.clear(); pr.clear();
         for (size_t k = 0; k < Hp.in_keys.size(); ++k) {
           int b = Hp.in_keys[k] / Hp.nd, d = Hp.in_keys[k] % Hp.nd;
@@ -847,8 +863,8 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
           specs.push_back(sp2);
         }
       F.l2l.M = F.R; F.l2l.Kd = Hp.R; F.l2l.nops = (int)specs.size();
-      F.l2l.ops = ar.alloc<float2>(std::max<size_t>(1, specs.size()) * F.R * Hp.R);
-      form_ops(kOpL2L, specs, dreps, F.R, Hp.R, F.l2l.ops, cb, ar, s);
+      F.l2l.ops = ar.alloc<float2>((std::max<size_t>(1, specs.size()) * F.R * Hp.R) * P->cw);
+      form_ops(kOpL2L, specs, dreps, F.R, Hp.R, F.l2l.ops, P->fp64, cb, ar, s);
       std::vector<int32_t> op;
       std::vector<int2> pr;
       for (size_t k = 0; k < Hp.in_keys.size(); ++k) {
@@ -866,6 +882,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
     }
   }
 
+  phase(3);
   // ---- per-point data: local coordinates, L2P rows, P2P lists, M2P rows
   std::vector<float4> loc(N), loc_lo(N);
   std::vector<int> leaf_level(N, -1);
@@ -915,14 +932,14 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
     F.l2p_jobs = upload(jobs, ar, s);
     F.n_l2p_rows = row;
     F.l2p_map = upload(rmap, ar, s);
-    F.l2p_rows = ar.alloc<float2>(std::max<int64_t>(1, row) * F.R);
-    F.p2m_rows = ar.alloc<float2>(std::max<int64_t>(1, row) * F.R);
+    F.l2p_rows = ar.alloc<float2>(std::max<int64_t>(1, row) * F.R * P->cw);
+    F.p2m_rows = ar.alloc<float2>(std::max<int64_t>(1, row) * F.R * P->cw);
     if (row > 0) {
       ArenaMark mk(ar);
       double* dlp = ar.alloc<double>(lp.size());
       DFMM_CUDA(cudaMemcpyAsync(dlp, lp.data(), lp.size() * 8, cudaMemcpyHostToDevice, s));
-      form_rows(true, dreps[ridx.at({l, -1})], dlp, row, F.l2p_rows, cb, ar, s);
-      form_p2m_rows(dreps[ridx.at({l, -1})], dlp, row, F.p2m_rows, cb, ar, s);
+      form_rows(true, dreps[ridx.at({l, -1})], dlp, row, F.l2p_rows, P->fp64, cb, ar, s);
+      form_p2m_rows(dreps[ridx.at({l, -1})], dlp, row, F.p2m_rows, P->fp64, cb, ar, s);
     }
     other_flops += 8.0 * F.r * (double)row;
   }
@@ -950,15 +967,16 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
     g.njobs = (int64_t)jobs.size();
     g.nrows = row;
     g.jobs = upload(jobs, ar, s);
-    g.rows = ar.alloc<float2>(row * g.R);
+    g.rows = ar.alloc<float2>(row * g.R * P->cw);
     {
       ArenaMark mk(ar);
       double* dlp = ar.alloc<double>(lp.size());
       DFMM_CUDA(cudaMemcpyAsync(dlp, lp.data(), lp.size() * 8, cudaMemcpyHostToDevice, s));
-      form_rows(false, dreps[ridx.at({la, -1})], dlp, row, g.rows, cb, ar, s);
+      form_rows(false, dreps[ridx.at({la, -1})], dlp, row, g.rows, P->fp64, cb, ar, s);
     }
     P->m2p.push_back(g);
   }
+  phase(4);
   // P2P lists (U), CSR per target leaf: per source leaf (first point, count,
   // offset of its points within the leaf's list, self) and the exact centre
   // offset c_src - c_tgt (a multiple of the finest half-width, exact in FP32)
@@ -1048,6 +1066,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
   P->stats.other_translation_flops = other_flops;
   P->stats.plan_bytes = (int64_t)ar.bytes() + (P->close_keep ? (int64_t)P->close_keep->bytes() : 0);
   P->stats.p2p_close_pairs = P->n_close;
+  phase(5);
   P->stats.plan_seconds = now() - t0;
 }
 
@@ -1092,9 +1111,10 @@ Workspace* get_workspace(dfmm_plan_s* P, cudaStream_t s, int nrhs) {
   W->nrhs = nrhs;
   DevArena& ar = W->ar;
   const int64_t N = P->N;
-  W->fs = ar.alloc<float2>(N * nrhs);
-  W->us = ar.alloc<float2>(N * nrhs);
-  W->zero.push_back({W->us, (size_t)N * nrhs * sizeof(float2)});
+  const int64_t cw = P->cw;   // float2 units per complex element
+  W->fs = ar.alloc<float2>(N * nrhs * cw);
+  W->us = ar.alloc<float2>(N * nrhs * cw);
+  W->zero.push_back({W->us, (size_t)N * nrhs * cw * sizeof(float2)});
   W->S.assign(P->nl, nullptr);
   W->T.assign(P->nl, nullptr);
   int64_t p2l_rows = 1;
@@ -1105,17 +1125,17 @@ Workspace* get_workspace(dfmm_plan_s* P, cudaStream_t s, int nrhs) {
     else if (P->l_top >= 0 && l >= P->l_top) {
       R = P->hf[l].R;
       int64_t so = (int64_t)P->hf[l].out_keys.size(), si = (int64_t)P->hf[l].in_keys.size();
-      if (so) { W->S[l] = ar.alloc<float2>(so * nrhs * R); W->zero_late.push_back({W->S[l], (size_t)so * nrhs * R * 8}); }
-      if (si) { W->T[l] = ar.alloc<float2>(si * nrhs * R); W->zero_late.push_back({W->T[l], (size_t)si * nrhs * R * 8}); }
+      if (so) { W->S[l] = ar.alloc<float2>(so * nrhs * R * cw); W->zero_late.push_back({W->S[l], (size_t)so * nrhs * R * 8 * cw}); }
+      if (si) { W->T[l] = ar.alloc<float2>(si * nrhs * R * cw); W->zero_late.push_back({W->T[l], (size_t)si * nrhs * R * 8 * cw}); }
       continue;
     } else continue;
-    W->S[l] = ar.alloc<float2>(rows * nrhs * R);
-    W->T[l] = ar.alloc<float2>(rows * nrhs * R);
-    W->zero.push_back({W->S[l], (size_t)rows * nrhs * R * 8});
-    W->zero.push_back({W->T[l], (size_t)rows * nrhs * R * 8});
+    W->S[l] = ar.alloc<float2>(rows * nrhs * R * cw);
+    W->T[l] = ar.alloc<float2>(rows * nrhs * R * cw);
+    W->zero.push_back({W->S[l], (size_t)rows * nrhs * R * 8 * cw});
+    W->zero.push_back({W->T[l], (size_t)rows * nrhs * R * 8 * cw});
     p2l_rows = std::max(p2l_rows, P->lf[l].n_p2l * 2 * R);
   }
-  W->p2l = ar.alloc<float2>(p2l_rows * nrhs);
+  W->p2l = ar.alloc<float2>(p2l_rows * nrhs * cw);
   if (P->opt.m2l_mode == 2) {
     // split arrays: 2 values per complex element, 2 bytes each (4 for the TF32 split)
     int64_t e = max_source_elems(P) * nrhs * 2 * (P->opt.tc_precision == 2 ? 2 : 1);
@@ -1294,7 +1314,8 @@ struct Runner {
       else launch_gemm_stage_tc(a, targs, W->status, s);
     } else {
       ProfScope ps(W, s, g.fam, g.flops_rhs * nrhs, g.bytes_fixed + g.bytes_rhs * nrhs);
-      launch_gemm_stage(a, s);
+      if (P->fp64) launch_gemm_stage64(a, s);
+      else launch_gemm_stage(a, s);
     }
   }
 };
@@ -1345,7 +1366,10 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
     if (ctl)   // the batched form resets every state in line
       for (auto& z : W->zero_late) DFMM_CUDA(cudaMemsetAsync(z.first, 0, z.second, s));
   }
-  R.at(kWaveStart).launch(F_PERMUTE, 0.0, 20.0 * N * nrhs, [&] { launch_permute_in(f, P->perm, N, nrhs, W->fs, s); });
+  R.at(kWaveStart).launch(F_PERMUTE, 0.0, 20.0 * N * nrhs, [&] {
+    if (P->fp64) launch_permute_in64(f, P->perm, N, nrhs, W->fs, s);
+    else launch_permute_in(f, P->perm, N, nrhs, W->fs, s);
+  });
   // 1. LF upward: P2M at leaves, LF-M2M from the level below
   for (int l = nl - 1; l >= P->l_lf0; --l) {
     LFLevel& F = P->lf[l];
@@ -1360,7 +1384,8 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
                  a.state = W->S[l];
                  a.R = F.R;
                  a.nrhs = nrhs;
-                 launch_p2m_rows(a, s);
+                 if (P->fp64) launch_p2m_rows64(a, s);
+                 else launch_p2m_rows(a, s);
                });
     }
     if (l + 1 < nl) R.at(wave_lf_m2m(lw(l))).gemm(F.m2m, S(l + 1), P->lf[l + 1].R, P->lf[l + 1].nbox, S(l), F.R, kSrcS + l + 1);
@@ -1401,7 +1426,7 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
     if (F.n_p2l) {
       double ev = (double)F.npts_x * 2 * F.r;
       R.at(wave_lf_down(lw(l), 2)).launch(F_P2L_EVAL, ev * (16 + 8.0 * nrhs), F.npts_x * (16.0 + 8.0 * nrhs) + F.n_p2l * 2.0 * F.R * 8 * nrhs, [&] {
-        P2CArgs a;
+        P2CArgs a{};
         a.jobs = F.p2l_jobs;
         a.njobs = F.n_p2l;
         a.shifts = F.p2l_shifts;
@@ -1412,7 +1437,10 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
         a.fs = W->fs;
         a.out = W->p2l;
         a.nrhs = nrhs;
-        launch_p2c(a, s);
+        a.chk64 = F.chk64;
+        a.pts_lo = P->pts_lo;
+        if (P->fp64) launch_p2c64(a, s);
+        else launch_p2c(a, s);
       });
       R.at(wave_lf_down(lw(l), 3)).gemm(F.p2l, count ? nullptr : W->p2l, 2 * F.R, F.n_p2l, T(l), F.R, -1);
     }
@@ -1430,7 +1458,8 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
       a.R = F.R;
       a.nrhs = nrhs;
       a.us = W->us;
-      launch_l2p(a, s);
+      if (P->fp64) launch_l2p64(a, s);
+      else launch_l2p(a, s);
     });
   }
   for (size_t k = 0; k < P->m2p.size(); ++k) {
@@ -1445,7 +1474,8 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
       a.nrhs = nrhs;
       a.us = W->us;
       a.atomic = 1;
-      launch_rows(a, s);
+      if (P->fp64) launch_rows64(a, s);
+      else launch_rows(a, s);
     });
   }
   // 6. near field
@@ -1465,10 +1495,14 @@ void run_apply(dfmm_plan_s* P, const float2* f, float2* u, int nrhs, cudaStream_
     a.close_off = P->close_off;
     a.close_j = P->close_j;
     a.close_w = P->close_w;
-    if (P->opt.p2p_mode == 2) launch_p2p_fast(a, N, s);
+    if (P->fp64) launch_p2p64(a, s);
+    else if (P->opt.p2p_mode == 2) launch_p2p_fast(a, N, s);
     else launch_p2p(a, s);
   });
-  R.at(kWaveEnd).launch(F_PERMUTE, 0.0, 20.0 * N * nrhs, [&] { launch_permute_out(W->us, P->perm, N, nrhs, u, s); });
+  R.at(kWaveEnd).launch(F_PERMUTE, 0.0, 20.0 * N * nrhs, [&] {
+    if (P->fp64) launch_permute_out64(W->us, P->perm, N, nrhs, u, s);
+    else launch_permute_out(W->us, P->perm, N, nrhs, u, s);
+  });
 }
 
 // Every translation stage of the plan, for laying out work tiles.
@@ -1493,20 +1527,21 @@ size_t carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaS
     return p;
   };
   const int64_t N = P->N;
+  const size_t cb = 8 * (size_t)P->cw;   // bytes per complex element
   W.external = true;
   W.nrhs = nrhs;
   // the device status word first, at offset 0 of the region (reset by every apply)
   W.status = (unsigned*)take(4);
   W.zero.push_back({W.status, 4});
-  W.fs = (float2*)take((size_t)N * nrhs * 8);
-  W.us = (float2*)take((size_t)N * nrhs * 8);
-  W.zero.push_back({W.us, (size_t)N * nrhs * 8});
+  W.fs = (float2*)take((size_t)N * nrhs * cb);
+  W.us = (float2*)take((size_t)N * nrhs * cb);
+  W.zero.push_back({W.us, (size_t)N * nrhs * cb});
   W.S.assign(P->nl, nullptr);
   W.T.assign(P->nl, nullptr);
   size_t p2l_rows = 1;
   for (int l = 0; l < P->nl; ++l) {
     if (l >= P->l_lf0) {
-      size_t b = (size_t)P->lf[l].nbox * nrhs * P->lf[l].R * 8;
+      size_t b = (size_t)P->lf[l].nbox * nrhs * P->lf[l].R * cb;
       W.S[l] = (float2*)take(b);
       W.T[l] = (float2*)take(b);
       W.zero.push_back({W.S[l], b});
@@ -1515,11 +1550,11 @@ size_t carve_workspace(dfmm_plan_s* P, int nrhs, char* base, size_t bytes, cudaS
     } else if (P->l_top >= 0 && l >= P->l_top) {
       size_t so = P->hf[l].out_keys.size(), si = P->hf[l].in_keys.size();
       size_t R = P->hf[l].R;
-      if (so) { W.S[l] = (float2*)take(so * nrhs * R * 8); W.zero.push_back({W.S[l], so * nrhs * R * 8}); }
-      if (si) { W.T[l] = (float2*)take(si * nrhs * R * 8); W.zero.push_back({W.T[l], si * nrhs * R * 8}); }
+      if (so) { W.S[l] = (float2*)take(so * nrhs * R * cb); W.zero.push_back({W.S[l], so * nrhs * R * cb}); }
+      if (si) { W.T[l] = (float2*)take(si * nrhs * R * cb); W.zero.push_back({W.T[l], si * nrhs * R * cb}); }
     }
   }
-  W.p2l = (float2*)take(p2l_rows * nrhs * 8);
+  W.p2l = (float2*)take(p2l_rows * nrhs * cb);
   if (P->opt.m2l_mode == 2) {
     size_t e = (size_t)max_source_elems(P) * nrhs * 2 * (P->opt.tc_precision == 2 ? 2 : 1);
     W.ahi = (__half*)take(e * 2);
@@ -1843,8 +1878,12 @@ int dfmm_plan(const double* points, int64_t N, double K, double eps, const dfmm_
     if (o.leaf_max <= 0) o.leaf_max = 64;
     if (o.sample_box <= 0) o.sample_box = 1024;
     if (o.sample_far <= 0) o.sample_far = 4096;
-    if (o.sketch_rows <= 0) o.sketch_rows = 400;
-    if (!(o.eps_op_factor > 0)) o.eps_op_factor = 0.3;
+    // eps below 1e-7 needs ranks up to about 320 (and 2r sketch rows)
+    if (o.sketch_rows <= 0) o.sketch_rows = eps >= 1e-7 ? 400 : 800;
+    // skeleton tolerance eps_op = factor * eps: 0.3 keeps the result within eps down to
+    // eps 1e-6; below 1e-7 the errors of more levels add up relative to eps, and
+    // 0.1 keeps it within eps at 1e-8
+    if (!(o.eps_op_factor > 0)) o.eps_op_factor = eps >= 1e-7 ? 0.3 : 0.1;
     if (o.m2l_mode < 0 || o.m2l_mode > 2) return fail(DFMM_ERR_INVALID, "m2l_mode must be 0, 1 or 2");
     // automatic form: the split-FP16 tensor-core form adds about 2e-6
     // relative error, so it serves eps >= 1e-5; tighter tolerances use FP32
@@ -1860,6 +1899,16 @@ int dfmm_plan(const double* points, int64_t N, double K, double eps, const dfmm_
     if (o.tc_precision < 0 || o.tc_precision > 2) return fail(DFMM_ERR_INVALID, "tc_precision must be 0, 1 or 2");
     if (o.tc_precision != 0 && o.tc_layout == 1)
       return fail(DFMM_ERR_INVALID, "the BF16 and TF32 splits need the split-complex form (tc_layout 0)");
+    if (o.arith != 0 && o.arith != 32 && o.arith != 64) return fail(DFMM_ERR_INVALID, "arith must be 0, 32 or 64");
+    // automatic arithmetic: the FP32 forms serve eps >= 1e-6; tighter
+    // tolerances compute in FP64 throughout (complex128 densities and potentials)
+    if (o.arith == 0) o.arith = eps >= 1e-6 ? 32 : 64;
+    if (o.arith == 64) {
+      if (opts && opts->m2l_mode == 2)
+        return fail(DFMM_ERR_INVALID, "the tensor-core translations are not part of the FP64 form (arith 64)");
+      o.m2l_mode = 1;   // translations on the CUDA cores, in FP64
+      o.p2p_mode = 1;   // no FP32 near field (and no close-pair pass)
+    }
     // automatic near field: FP32 coordinates with exact close-pair
     // corrections for eps >= 1e-5, double-float coordinates below
     if (o.p2p_mode == 0) o.p2p_mode = eps >= 1e-5 ? 2 : 1;
@@ -1870,6 +1919,9 @@ int dfmm_plan(const double* points, int64_t N, double K, double eps, const dfmm_
     P->W = std::pow(2.0, std::max(0.0, std::ceil(std::log2(K))));
     P->eps = eps;
     P->opt = o;
+    P->fp64 = o.arith == 64;
+    P->cw = P->fp64 ? 2 : 1;
+    P->stats.arith = o.arith;
     P->eps_op = eps * o.eps_op_factor;
     P->stats.N = N;
     P->stats.K = K;
@@ -1880,7 +1932,13 @@ int dfmm_plan(const double* points, int64_t N, double K, double eps, const dfmm_
     DFMM_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     struct SG { cudaStream_t s; ~SG() { cudaStreamDestroy(s); } } sg{s};
     build_plan(P.get(), points, s);
-    if (P->opt.m2l_mode == 2) build_images(P.get(), s);
+    if (P->opt.m2l_mode == 2) {
+      const double ti = now();
+      build_images(P.get(), s);
+      DFMM_CUDA(cudaStreamSynchronize(s));
+      P->stats.plan_phase_seconds[6] = now() - ti;
+      P->stats.plan_seconds += P->stats.plan_phase_seconds[6];
+    }
     DFMM_CUDA(cudaStreamSynchronize(s));
     *out = P.release();
     return DFMM_OK;
@@ -1902,10 +1960,10 @@ int dfmm_apply_host(dfmm_plan_t plan, const void* f_host, void* u_host, int nrhs
     if (!plan || !f_host || !u_host) return fail(DFMM_ERR_INVALID, "null argument");
     if (nrhs < 1 || nrhs > 64) return fail(DFMM_ERR_INVALID, "nrhs must be in [1, 64]");
     Workspace* W = get_workspace(plan, stream, nrhs);
-    size_t bytes = (size_t)plan->N * nrhs * sizeof(float2);
+    size_t bytes = (size_t)plan->N * nrhs * sizeof(float2) * plan->cw;
     if (!W->f_dev) {
-      W->f_dev = W->ar.alloc<float2>(plan->N * W->nrhs);
-      W->u_dev = W->ar.alloc<float2>(plan->N * W->nrhs);
+      W->f_dev = W->ar.alloc<float2>(plan->N * W->nrhs * plan->cw);
+      W->u_dev = W->ar.alloc<float2>(plan->N * W->nrhs * plan->cw);
     }
     DFMM_CUDA(cudaMemcpyAsync(W->f_dev, f_host, bytes, cudaMemcpyHostToDevice, stream));
     run_apply(plan, W->f_dev, W->u_dev, nrhs, stream);

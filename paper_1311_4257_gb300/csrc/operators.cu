@@ -3,7 +3,7 @@
 // Every operator is a product of bounded factors (an orthonormal projection,
 // the kernel matrix between check and equivalent points, and the inverse
 // triangular factor of the source basis), formed in FP64 and rounded once to
-// complex64 for the apply kernels.  The kernel matrices are evaluated by a
+// complex64 for the apply kernels (kept in complex128 for the FP64 form).  The kernel matrices are evaluated by a
 // hand-written FP64 kernel; the two small products per operator are plain
 // batched ZGEMMs (cuBLAS).
 #include <cmath>
@@ -73,6 +73,18 @@ __global__ void to_c64_kernel(const double2* __restrict__ in, float2* __restrict
   if (i < n) out[i] = make_float2((float)in[i].x, (float)in[i].y);
 }
 
+// n FP64 results to elements [at, at + n) of out: rounded once to complex64,
+// or copied as they are when the plan computes in FP64 (complex128 out)
+void store_out(const double2* in, void* out, int64_t at, int64_t n, bool fp64, cudaStream_t s) {
+  if (n <= 0) return;
+  if (fp64) {
+    DFMM_CUDA(cudaMemcpyAsync((double2*)out + at, in, n * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+  } else {
+    to_c64_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(in, (float2*)out + at, n);
+    DFMM_CUDA(cudaGetLastError());
+  }
+}
+
 // row-major C (m x n) = A (m x k) B (k x n), batched through pointer arrays
 void gemm_rm_batched(cublasHandle_t cb, int m, int n, int k, const double2** A, const double2** B, double2** C,
                      int batch) {
@@ -132,7 +144,7 @@ DevRep upload_rep(const Rep& rep, int R, DevArena& ar, cudaStream_t s) {
 }
 
 void form_ops(OpKind kind, const std::vector<OpSpec>& ops, const std::vector<DevRep>& reps, int Rt, int Rs,
-              float2* out, cublasHandle_t cb, DevArena& ar, cudaStream_t s) {
+              void* out, bool fp64, cublasHandle_t cb, DevArena& ar, cudaStream_t s) {
   if (ops.empty()) return;
   ArenaMark mark(ar);
   DevRep* d_reps = ar.alloc<DevRep>(reps.size());
@@ -184,15 +196,13 @@ void form_ops(OpKind kind, const std::vector<OpSpec>& ops, const std::vector<Dev
     DFMM_CUDA(cudaMemcpyAsync(pB, hB.data(), nb * sizeof(void*), cudaMemcpyHostToDevice, s));
     DFMM_CUDA(cudaMemcpyAsync(pC, hC.data(), nb * sizeof(void*), cudaMemcpyHostToDevice, s));
     gemm_rm_batched(cb, Rt, Rs, Rs, pA, pB, pC, nb);
-    int64_t ne = (int64_t)nb * Rt * Rs;
-    to_c64_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(T2, out + start * (size_t)Rt * Rs, ne);
-    DFMM_CUDA(cudaGetLastError());
+    store_out(T2, out, (int64_t)start * Rt * Rs, (int64_t)nb * Rt * Rs, fp64, s);
     DFMM_CUDA(cudaStreamSynchronize(s));
   }
 }
 
-void form_rows(bool incoming, const DevRep& rep, const double* d_pts, int64_t n, float2* out, cublasHandle_t cb,
-               DevArena& ar, cudaStream_t s) {
+void form_rows(bool incoming, const DevRep& rep, const double* d_pts, int64_t n, void* out, bool fp64,
+               cublasHandle_t cb, DevArena& ar, cudaStream_t s) {
   if (n <= 0) return;
   ArenaMark mark(ar);
   int R = rep.R;
@@ -210,14 +220,13 @@ void form_rows(bool incoming, const DevRep& rep, const double* d_pts, int64_t n,
     // row-major T (m x R) = K (m x R) Rinv (R x R)
     DFMM_CUBLAS(cublasZgemm(cb, CUBLAS_OP_N, CUBLAS_OP_N, R, (int)m, R, &one, (const cuDoubleComplex*)Rinv, R,
                             (const cuDoubleComplex*)K, R, &zero, (cuDoubleComplex*)T, R));
-    to_c64_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(T, out + st * R, ne);
-    DFMM_CUDA(cudaGetLastError());
+    store_out(T, out, st * R, ne, fp64, s);
   }
   DFMM_CUDA(cudaStreamSynchronize(s));
 }
 
-void form_p2m_rows(const DevRep& rep, const double* d_pts, int64_t n, float2* out, cublasHandle_t cb, DevArena& ar,
-                   cudaStream_t s) {
+void form_p2m_rows(const DevRep& rep, const double* d_pts, int64_t n, void* out, bool fp64, cublasHandle_t cb,
+                   DevArena& ar, cudaStream_t s) {
   if (n <= 0) return;
   ArenaMark mark(ar);
   const int R = rep.R, K2 = 2 * R;
@@ -235,8 +244,7 @@ void form_p2m_rows(const DevRep& rep, const double* d_pts, int64_t n, float2* ou
     // row-major T (m x R) = K (m x 2R) PoutH^T, PoutH = Qo^H W (R x 2R, row-major)
     DFMM_CUBLAS(cublasZgemm(cb, CUBLAS_OP_T, CUBLAS_OP_N, R, (int)m, K2, &one, (const cuDoubleComplex*)rep.PoutH,
                             K2, (const cuDoubleComplex*)K, K2, &zero, (cuDoubleComplex*)T, R));
-    to_c64_kernel<<<(unsigned)((m * R + 255) / 256), 256, 0, s>>>(T, out + st * R, m * R);
-    DFMM_CUDA(cudaGetLastError());
+    store_out(T, out, st * R, m * R, fp64, s);
   }
   DFMM_CUDA(cudaStreamSynchronize(s));
 }

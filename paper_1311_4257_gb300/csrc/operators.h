@@ -37,22 +37,24 @@ struct OpSpec {
 };
 
 // Forms ops (all of one kind, one pair of width classes R_t, R_s) and writes
-// them as complex64 [n][R_t][R_s] into out (device).
+// them as complex64 [n][R_t][R_s] into out (device), or as complex128 when
+// fp64 is set (the FP64 form of the apply).
 void form_ops(OpKind kind, const std::vector<OpSpec>& ops, const std::vector<DevRep>& reps, int Rt, int Rs,
-              float2* out, cublasHandle_t cb, DevArena& ar, cudaStream_t s);
+              void* out, bool fp64, cublasHandle_t cb, DevArena& ar, cudaStream_t s);
 
 // Rows for evaluating a representation at points:
 //   L2P (incoming): row_i = G(y_i - c, a_in) W Ri^{-1}
 //   M2P (outgoing): row_i = G(y_i - c, b) Ro^{-1}
-// pts: device FP64 [n][3] of y_i - c (local), written as complex64 [n][R].
-void form_rows(bool incoming, const DevRep& rep, const double* d_local_pts, int64_t n, float2* out,
+// pts: device FP64 [n][3] of y_i - c (local), written as complex64 [n][R]
+// (complex128 when fp64 is set).
+void form_rows(bool incoming, const DevRep& rep, const double* d_local_pts, int64_t n, void* out, bool fp64,
                cublasHandle_t cb, DevArena& ar, cudaStream_t s);
 
 // Rows of P2M through the outgoing representation (Eq. 2 with the
 // least-squares projection): row_i = Qo^H W G(a2, y_i - c), the outgoing
 // state a unit source at y_i produces.  pts: device FP64 [n][3] of y_i - c;
-// written as complex64 [n][R].
-void form_p2m_rows(const DevRep& rep, const double* d_local_pts, int64_t n, float2* out, cublasHandle_t cb,
+// written as complex64 [n][R] (complex128 when fp64 is set).
+void form_p2m_rows(const DevRep& rep, const double* d_local_pts, int64_t n, void* out, bool fp64, cublasHandle_t cb,
                    DevArena& ar, cudaStream_t s);
 
 }  // namespace dfmm

@@ -35,6 +35,9 @@ double now_s() {
 
 size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
 
+// bytes of one density or potential value: complex64, or complex128 for an FP64 plan
+size_t elem_bytes(const dfmm_stats& st) { return st.arith == 64 ? 16 : 8; }
+
 struct Request {
   int64_t ticket = 0;
   dfmm_plan_t plan = nullptr;
@@ -133,7 +136,7 @@ struct dfmm_server_s {
     }
     dfmm_stats st{};
     dfmm_plan_stats(plan, &st);
-    return 2 * align256((size_t)st.N * nrhs * 8) + align256(it->second) + 256;
+    return 2 * align256((size_t)st.N * nrhs * elem_bytes(st)) + align256(it->second) + 256;
   }
 
   void finish(Slot& sl, int status) {   // under mu
@@ -170,15 +173,16 @@ struct dfmm_server_s {
     dfmm_stats st{};
     dfmm_plan_stats(plan, &st);
     const size_t N = (size_t)st.N;
+    const size_t eb = elem_bytes(st);
     char* p = base + sl.off;
-    float2* f_dev = (float2*)p;
-    float2* u_dev = (float2*)(p + align256(N * total_rhs * 8));
-    char* scratch = p + 2 * align256(N * total_rhs * 8);
-    const size_t scratch_bytes = sl.bytes - 2 * align256(N * total_rhs * 8);
+    char* f_dev = p;
+    char* u_dev = p + align256(N * total_rhs * eb);
+    char* scratch = p + 2 * align256(N * total_rhs * eb);
+    const size_t scratch_bytes = sl.bytes - 2 * align256(N * total_rhs * eb);
     int rc = DFMM_OK;
     size_t k = 0;
     for (auto& r : sl.group) {
-      if (cudaMemcpyAsync(f_dev + k * N, r->f_host, N * r->nrhs * 8, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
+      if (cudaMemcpyAsync(f_dev + k * N * eb, r->f_host, N * r->nrhs * eb, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
         rc = DFMM_ERR_CUDA;
       k += r->nrhs;
     }
@@ -186,7 +190,7 @@ struct dfmm_server_s {
     if (rc == DFMM_OK) {
       k = 0;
       for (auto& r : sl.group) {
-        if (cudaMemcpyAsync(r->u_host, u_dev + k * N, N * r->nrhs * 8, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
+        if (cudaMemcpyAsync(r->u_host, u_dev + k * N * eb, N * r->nrhs * eb, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess)
           rc = DFMM_ERR_CUDA;
         k += r->nrhs;
       }

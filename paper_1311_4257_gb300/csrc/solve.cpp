@@ -57,6 +57,7 @@ extern "C" int dfmm_solve(dfmm_plan_t plan, double alpha_re, double alpha_im, do
     if (!(tol > 0)) return dfmm::set_error(DFMM_ERR_INVALID, "tol must be positive");
     dfmm_stats st{};
     dfmm_plan_stats(plan, &st);
+    if (st.arith != 32) return dfmm::set_error(DFMM_ERR_UNSUPPORTED, "dfmm_solve takes plans that compute in FP32");
     const int64_t N = st.N;
     const int m = restart;
     const cd alpha(alpha_re, alpha_im), beta(beta_re, beta_im);

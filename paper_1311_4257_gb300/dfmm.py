@@ -33,7 +33,8 @@ class Options(ctypes.Structure):
                 ("sketch_rows", ctypes.c_int32), ("eps_op_factor", ctypes.c_double), ("m2l_mode", ctypes.c_int32),
                 ("host_threads", ctypes.c_int32), ("cache_dir", ctypes.c_char_p), ("tc_stages", ctypes.c_int32),
                 ("wait_test", ctypes.c_int32), ("tile_order", ctypes.c_int32), ("p2p_mode", ctypes.c_int32),
-                ("tc_layout", ctypes.c_int32), ("tc_accumulate", ctypes.c_int32), ("tc_precision", ctypes.c_int32)]
+                ("tc_layout", ctypes.c_int32), ("tc_accumulate", ctypes.c_int32), ("tc_precision", ctypes.c_int32),
+                ("arith", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -46,14 +47,16 @@ class Stats(ctypes.Structure):
                 ("w_pairs", ctypes.c_int64), ("x_pairs", ctypes.c_int64), ("p2p_interactions", ctypes.c_int64),
                 ("plan_bytes", ctypes.c_int64), ("plan_seconds", ctypes.c_double), ("m2l_flops", ctypes.c_double),
                 ("other_translation_flops", ctypes.c_double), ("hf_ops", ctypes.c_int64 * 32),
-                ("p2p_close_pairs", ctypes.c_int64)]
+                ("p2p_close_pairs", ctypes.c_int64), ("arith", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("plan_phase_seconds", ctypes.c_double * 8)]
 
     def to_dict(self) -> dict:
         n = self.n_levels
         d = {}
         for name, _ in self._fields_:
             v = getattr(self, name)
-            d[name] = list(v)[:n] if hasattr(v, "__len__") else v
+            # per-level arrays (32 slots) hold n_levels entries
+            d[name] = (list(v)[:n] if len(v) == 32 else list(v)) if hasattr(v, "__len__") else v
         return d
 
 
@@ -178,7 +181,7 @@ class Plan:
                  sketch_rows: int = 0, eps_op_factor: float = 0.0, host_threads: int = 0,
                  cache_dir: str | None = None, m2l_mode: int = 0, tc_stages: int = 0, wait_test: int = 0,
                  tile_order: int = 0, p2p_mode: int = 0, tc_layout: int = 0,
-                 tc_accumulate: int = 0, tc_precision: int = 0):
+                 tc_accumulate: int = 0, tc_precision: int = 0, arith: int = 0):
         import torch
         if not (isinstance(points, torch.Tensor) and points.is_cuda):
             points = torch.as_tensor(np.ascontiguousarray(points, dtype=np.float64), device="cuda")
@@ -189,18 +192,24 @@ class Plan:
         self.K = float(K)
         self.eps = float(eps)
         o = Options(leaf_max, sample_box, sample_far, sketch_rows, eps_op_factor, m2l_mode, host_threads,
-                    cache_dir.encode() if cache_dir else None, tc_stages, wait_test, tile_order, p2p_mode, tc_layout, tc_accumulate, tc_precision)
+                    cache_dir.encode() if cache_dir else None, tc_stages, wait_test, tile_order, p2p_mode, tc_layout, tc_accumulate, tc_precision,
+                    arith)
         h = ctypes.c_void_p()
         _check(lib().dfmm_plan(points.data_ptr(), self.N, self.K, self.eps, ctypes.byref(o), ctypes.byref(h)))
         self._h = h
+        # element type of densities and potentials: complex128 when the plan computes in FP64
+        self.arith = int(self.stats()["arith"])
+        self.dtype = torch.complex128 if self.arith == 64 else torch.complex64
+        self.np_dtype = np.complex128 if self.arith == 64 else np.complex64
 
     def apply(self, f, u=None, stream=None):
-        """u = G f.  f: cuda complex64 [nrhs, N] (or [N]); returns u (same shape)."""
+        """u = G f.  f: cuda complex64 [nrhs, N] (or [N]), complex128 for an FP64 plan
+        (self.dtype); returns u (same shape)."""
         import torch
         squeeze = f.ndim == 1
         f2 = f.reshape(1, -1) if squeeze else f
-        if f2.dtype != torch.complex64 or not f2.is_cuda:
-            raise TypeError("f must be a cuda complex64 tensor")
+        if f2.dtype != self.dtype or not f2.is_cuda:
+            raise TypeError(f"f must be a cuda {self.dtype} tensor")
         f2 = f2.contiguous()
         nrhs = int(f2.shape[0])
         if f2.shape[1] != self.N:
@@ -211,8 +220,9 @@ class Plan:
         return u.reshape(-1) if squeeze else u
 
     def apply_host(self, f: np.ndarray, stream=None) -> np.ndarray:
-        """Host-buffer matvec: f numpy complex64 [nrhs, N] -> u numpy complex64."""
-        f2 = np.ascontiguousarray(np.atleast_2d(f), dtype=np.complex64)
+        """Host-buffer matvec: f numpy complex64 [nrhs, N] -> u numpy complex64
+        (complex128 for an FP64 plan)."""
+        f2 = np.ascontiguousarray(np.atleast_2d(f), dtype=self.np_dtype)
         u = np.empty_like(f2)
         _check(lib().dfmm_apply_host(self._h, f2.ctypes.data, u.ctypes.data, int(f2.shape[0]),
                                      _stream_ptr(stream)))
@@ -254,8 +264,8 @@ class Plan:
         """dfmm_graph_create: capture the apply u = G f on these buffers."""
         import torch
         f2 = f.reshape(1, -1) if f.ndim == 1 else f
-        if f2.dtype != torch.complex64 or not f2.is_cuda or not f2.is_contiguous() or f2.shape[1] != self.N:
-            raise TypeError("f must be a contiguous cuda complex64 [nrhs, N] tensor")
+        if f2.dtype != self.dtype or not f2.is_cuda or not f2.is_contiguous() or f2.shape[1] != self.N:
+            raise TypeError(f"f must be a contiguous cuda {self.dtype} [nrhs, N] tensor")
         if u.shape != f.shape or u.dtype != f.dtype or not u.is_contiguous():
             raise TypeError("u must match f")
         h = ctypes.c_void_p()
@@ -331,8 +341,8 @@ def apply_batched(plans, fs, us=None, stream=None):
         raise ValueError("one density tensor per plan")
     fs = [f.reshape(1, -1) if f.ndim == 1 else f for f in fs]
     for p, f in zip(plans, fs):
-        if f.dtype != torch.complex64 or not f.is_cuda or not f.is_contiguous() or f.shape[1] != p.N:
-            raise TypeError("each f must be a contiguous cuda complex64 [nrhs, N] tensor of its plan")
+        if f.dtype != p.dtype or not f.is_cuda or not f.is_contiguous() or f.shape[1] != p.N:
+            raise TypeError("each f must be a contiguous cuda [nrhs, N] tensor of its plan's dtype")
     if us is None:
         us = [torch.empty_like(f) for f in fs]
     vp = ctypes.c_void_p
@@ -357,8 +367,8 @@ class Batch:
         n = len(plans)
         fs = [f.reshape(1, -1) if f.ndim == 1 else f for f in fs]
         for p, f in zip(plans, fs):
-            if f.dtype != torch.complex64 or not f.is_cuda or not f.is_contiguous() or f.shape[1] != p.N:
-                raise TypeError("each f must be a contiguous cuda complex64 [nrhs, N] tensor of its plan")
+            if f.dtype != p.dtype or not f.is_cuda or not f.is_contiguous() or f.shape[1] != p.N:
+                raise TypeError("each f must be a contiguous cuda [nrhs, N] tensor of its plan's dtype")
         self.plans, self.fs = list(plans), fs
         self.us = us if us is not None else [torch.empty_like(f) for f in fs]
         vp = ctypes.c_void_p
@@ -397,7 +407,8 @@ class Batch:
 class Server:
     """dfmm_server_*: continuous batching of matvec requests over resident plans.
 
-    submit() takes host complex64 buffers [nrhs, N] (pinned torch tensors keep
+    submit() takes host complex64 buffers [nrhs, N] (complex128 for a plan whose
+    dtype is complex128; pinned torch tensors keep
     the copies asynchronous); the caller keeps them alive until wait() returns."""
 
     def __init__(self, streams: int = 4, budget_bytes: int = 8 << 30, max_rhs: int = 16):
