@@ -108,6 +108,10 @@ typedef struct {
                               1e-8.  With 64, f and u of every apply entry point are complex128
                               [nrhs][N], m2l_mode 2 is refused and the other m2l / p2p / tc
                               options are ignored; dfmm_solve takes arith 32 plans only. */
+  int32_t skeleton_host;   /* [0] where the skeleton pivot selection (Sec. 2.1: pivoted QR of the
+                              random sketch, then of the far samples) runs: 0 = on the GPU for all
+                              representation types of the plan at once; 1 = host threads
+                              (host_threads).  The samples, draws and pivot rule are the same. */
 } dfmm_options;
 
 /* Build a plan (Sec. 2.2 octree, lists, Eq. 2 representations and the
@@ -180,6 +184,11 @@ typedef struct {
                                      3 = translation operators (M2M, M2L, L2L, P2L projections);
                                      4 = per-point rows (L2P, P2M, M2P); 5 = near-field lists and
                                      close pairs; 6 = tensor-core operator images; 7 = unused */
+  double skeleton_phase_seconds[4]; /* phase 1 in detail: 0 = disk cache and samples; 1 = sketch pivots
+                                       (the whole host build in the host form); 2 = check-point
+                                       pivots; 3 = least-squares factors */
+  int64_t skeleton_types;           /* representation types built or loaded (canonical, up to the
+                                       cube's symmetries) */
 } dfmm_stats;
 
 int dfmm_plan_stats(dfmm_plan_t plan, dfmm_stats* out);
@@ -413,6 +422,16 @@ int64_t dfmm_apply_launches(dfmm_plan_t plan, int nrhs);
  *   cap     : capacity of b2/a2 in points; DFMM_ERR_INVALID if 2r > cap. */
 int dfmm_representation(double w, int cell, double w_top, double eps_op, int sample_box, int sample_far,
                         int sketch_rows, int* r_out, double* b2, double* a2, int cap);
+
+/* dfmm_representation with the two pivot selections (the column-pivoted QR of
+ * the +-1 sketch and the two QRs that pick the far check points) on the
+ * current GPU, the way dfmm_plan runs them unless options.skeleton_host is
+ * set.  Samples and sketch draws are the host's; the FP64 rounding differs,
+ * so pivots that nearly tie may differ from dfmm_representation's (either
+ * result is a valid skeleton).  Synchronises the device; same arguments and
+ * errors as dfmm_representation. */
+int dfmm_representation_device(double w, int cell, double w_top, double eps_op, int sample_box, int sample_far,
+                               int sketch_rows, int* r_out, double* b2, double* a2, int cap);
 
 /* Measured peak rates of the current GPU, for roofline denominators (the
  * paper has no counterpart).  Each rate comes from a short probe kernel of

@@ -15,7 +15,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdfmm.so")
 
-SOURCES = ["sort.cu", "tree.cu", "operators.cu", "apply.cu", "apply64.cu", "m2l_tc.cu", "m2l_cx.cu", "noalloc.cu", "probes.cu", "skeleton.cpp", "dfmm.cpp",
+SOURCES = ["sort.cu", "tree.cu", "operators.cu", "apply.cu", "apply64.cu", "skeleton_gpu.cu", "m2l_tc.cu", "m2l_cx.cu", "noalloc.cu", "probes.cu", "skeleton.cpp", "dfmm.cpp",
            "serve.cpp", "solve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

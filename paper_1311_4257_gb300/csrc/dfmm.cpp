@@ -530,7 +530,8 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
   sp.S_Y = P->opt.sample_box;
   sp.S_X = P->opt.sample_far;
   sp.sketch = P->opt.sketch_rows;
-  P->reps.reset(new RepSet(sp, w_top, P->opt.host_threads, P->opt.cache_dir ? P->opt.cache_dir : ""));
+  P->reps.reset(new RepSet(sp, w_top, P->opt.host_threads, P->opt.cache_dir ? P->opt.cache_dir : "",
+                           P->opt.skeleton_host == 0));
   std::vector<std::vector<int>> level_cells(nl);
   std::vector<std::pair<double, int>> need;
   for (int l = (has_hf ? P->l_top : P->l_lf0); l < nl; ++l) {
@@ -546,6 +547,8 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
   }
   P->reps->prepare(need);
   phase(1);
+  for (int k = 0; k < 4; ++k) P->stats.skeleton_phase_seconds[k] = P->reps->seconds[k];
+  P->stats.skeleton_types = (int64_t)P->reps->built();
   std::vector<DevRep> dreps;
   std::map<std::pair<int, int>, int> ridx;   // (level, cell) -> dreps index
   for (int l = (has_hf ? P->l_top : P->l_lf0); l < nl; ++l) {
@@ -1900,6 +1903,7 @@ int dfmm_plan(const double* points, int64_t N, double K, double eps, const dfmm_
     if (o.tc_precision != 0 && o.tc_layout == 1)
       return fail(DFMM_ERR_INVALID, "the BF16 and TF32 splits need the split-complex form (tc_layout 0)");
     if (o.arith != 0 && o.arith != 32 && o.arith != 64) return fail(DFMM_ERR_INVALID, "arith must be 0, 32 or 64");
+    if (o.skeleton_host < 0 || o.skeleton_host > 1) return fail(DFMM_ERR_INVALID, "skeleton_host must be 0 or 1");
     // automatic arithmetic: the FP32 forms serve eps >= 1e-6; tighter
     // tolerances compute in FP64 throughout (complex128 densities and potentials)
     if (o.arith == 0) o.arith = eps >= 1e-6 ? 32 : 64;
@@ -2342,8 +2346,12 @@ int64_t dfmm_apply_launches(dfmm_plan_t plan, int nrhs) {
   return c;
 }
 
-int dfmm_representation(double w, int cell, double w_top, double eps_op, int sample_box, int sample_far,
-                        int sketch_rows, int* r_out, double* b2, double* a2, int cap) {
+}  // extern "C"
+
+namespace {
+
+int representation_impl(bool on_device, double w, int cell, double w_top, double eps_op, int sample_box,
+                        int sample_far, int sketch_rows, int* r_out, double* b2, double* a2, int cap) {
   return guarded([&]() -> int {
     if (!r_out) return fail(DFMM_ERR_INVALID, "r_out is NULL");
     if (!(w > 0) || !(w_top >= 1) || !(eps_op > 0)) return fail(DFMM_ERR_INVALID, "bad representation arguments");
@@ -2354,7 +2362,21 @@ int dfmm_representation(double w, int cell, double w_top, double eps_op, int sam
     sp.S_Y = sample_box > 0 ? sample_box : 1024;
     sp.S_X = sample_far > 0 ? sample_far : 4096;
     sp.sketch = sketch_rows > 0 ? sketch_rows : 400;
-    Rep r = build_rep(w, cell, w_top, sp);
+    Rep r;
+    if (on_device) {
+      const Samples sm = make_samples(w, cell, w_top, sp);
+      std::vector<SketchJob> sj(1);
+      sj[0].sm = &sm;
+      sketch_pivots_device(sj, sp);
+      std::vector<CheckJob> cj(1);
+      cj[0].sm = &sm;
+      cj[0].r = rank_from_pivots(sj[0].diag, (int)sj[0].piv.size(), sp);
+      cj[0].b = box_points(sm, sj[0].piv, cj[0].r);
+      check_pivots_device(cj);
+      r = finish_rep(sm, sj[0].piv, cj[0].r, cj[0].p1, cj[0].p2);
+    } else {
+      r = build_rep(w, cell, w_top, sp);
+    }
     *r_out = r.r;
     if (b2 || a2) {
       if (2 * r.r > cap) return fail(DFMM_ERR_INVALID, "buffer capacity below 2r");
@@ -2363,6 +2385,20 @@ int dfmm_representation(double w, int cell, double w_top, double eps_op, int sam
     }
     return DFMM_OK;
   });
+}
+
+}  // namespace
+
+extern "C" {
+
+int dfmm_representation(double w, int cell, double w_top, double eps_op, int sample_box, int sample_far,
+                        int sketch_rows, int* r_out, double* b2, double* a2, int cap) {
+  return representation_impl(false, w, cell, w_top, eps_op, sample_box, sample_far, sketch_rows, r_out, b2, a2, cap);
+}
+
+int dfmm_representation_device(double w, int cell, double w_top, double eps_op, int sample_box, int sample_far,
+                               int sketch_rows, int* r_out, double* b2, double* a2, int cap) {
+  return representation_impl(true, w, cell, w_top, eps_op, sample_box, sample_far, sketch_rows, r_out, b2, a2, cap);
 }
 
 }  // extern "C"

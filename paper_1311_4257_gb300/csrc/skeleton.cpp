@@ -15,6 +15,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
+#include <functional>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -322,77 +324,61 @@ std::vector<cd> tri_inv(const std::vector<cd>& R, int n) {
   return X;
 }
 
-Rep build_from_samples(const std::vector<double>& Y, int SY, const std::vector<double>& X, int SX,
-                       const SkelParams& prm, uint64_t sketch_seed, double w, int cell) {
-  std::vector<double> Wx(SX);
-  for (int i = 0; i < SX; ++i) Wx[i] = norm3(&X[i * 3]);
-  // Z = Omega (Wx G(X, Y)); Omega +-1 from SplitMix draws, row-major order
-  int s = prm.sketch;
+}  // namespace
+
+// Stage 1 of the selection (host form): Z = Omega (Wx G(X, Y)) with Omega the
+// +-1 sketch from SplitMix draws (row-major order, draw k = q SX + i + 1),
+// then its column-pivoted QR over all sketch rows.
+void sketch_pivots_host(const Samples& sm, const SkelParams& prm, std::vector<int>& piv, std::vector<double>& diag) {
+  const int SX = sm.SX, SY = sm.SY, s = prm.sketch;
+  const std::vector<double>& X = sm.X;
+  const std::vector<double>& Y = sm.Y;
   std::vector<cd> A((size_t)SX * SY);
   for (int i = 0; i < SX; ++i)
-    for (int j = 0; j < SY; ++j) A[(size_t)i * SY + j] = Wx[i] * kernel(&X[i * 3], &Y[j * 3]);
+    for (int j = 0; j < SY; ++j) A[(size_t)i * SY + j] = sm.Wx[i] * kernel(&X[i * 3], &Y[j * 3]);
   std::vector<cd> Z((size_t)s * SY, cd(0, 0));
   for (int q = 0; q < s; ++q) {
     cd* zr = &Z[(size_t)q * SY];
     for (int i = 0; i < SX; ++i) {
       uint64_t kk = (uint64_t)q * SX + i + 1;
-      uint64_t z = splitmix64(sketch_seed + kk * GAMMA);
+      uint64_t z = splitmix64(sm.sketch_seed + kk * GAMMA);
       const cd* ar = &A[(size_t)i * SY];
       if ((z >> 63) == 0) for (int j = 0; j < SY; ++j) zr[j] += ar[j];
       else for (int j = 0; j < SY; ++j) zr[j] -= ar[j];
     }
   }
-  std::vector<int> piv;
-  std::vector<double> diag;
   pivoted_qr(Z, s, SY, 0.0, s, piv, diag);
-  int r = 0;
-  for (double d : diag) if (d > prm.eps_op * diag[0]) ++r;
-  if (2 * r > (int)piv.size()) throw std::runtime_error("representation rank too large for the sketch");
-  Rep rep;
-  rep.w = w;
-  rep.cell = cell;
-  rep.r = r;
-  rep.b2.resize((size_t)2 * r * 3);
-  for (int q = 0; q < 2 * r; ++q)
-    for (int d = 0; d < 3; ++d) rep.b2[q * 3 + d] = Y[piv[q] * 3 + d];
-  // A2 = (Wx G(X, b))^T : r x SX
+}
+
+// Stage 2 (host form): the 2r far check points.  A2 = (Wx G(X, b))^T (r x SX);
+// the first r are its pivots p1, the next r the pivots p2 of A2 restricted to
+// the columns not in p1 (in ascending order).
+void check_pivots_host(const Samples& sm, const std::vector<double>& b, int r, std::vector<int>& p1,
+                       std::vector<int>& p2) {
+  const int SX = sm.SX;
+  std::vector<double> diag;
   std::vector<cd> A2((size_t)r * SX);
   for (int i = 0; i < SX; ++i)
-    for (int q = 0; q < r; ++q) A2[(size_t)q * SX + i] = Wx[i] * kernel(&X[i * 3], &rep.b2[q * 3]);
+    for (int q = 0; q < r; ++q) A2[(size_t)q * SX + i] = sm.Wx[i] * kernel(&sm.X[i * 3], &b[q * 3]);
   std::vector<cd> A2c = A2;
-  std::vector<int> p1, p2;
   pivoted_qr(A2c, r, SX, 0.0, r, p1, diag);
-  std::vector<char> used(SX, 0);
-  for (int p : p1) used[p] = 1;
-  std::vector<int> rest;
-  for (int i = 0; i < SX; ++i) if (!used[i]) rest.push_back(i);
+  const std::vector<int> rest = rest_of(p1, SX);
   std::vector<cd> A3((size_t)r * rest.size());
   for (int q = 0; q < r; ++q)
     for (size_t c = 0; c < rest.size(); ++c) A3[(size_t)q * rest.size() + c] = A2[(size_t)q * SX + rest[c]];
   pivoted_qr(A3, r, (int)rest.size(), 0.0, r, p2, diag);
-  if ((int)p1.size() != r || (int)p2.size() != r) throw std::runtime_error("check-point selection failed");
-  rep.a2.resize((size_t)2 * r * 3);
-  rep.wa2.resize(2 * r);
-  for (int q = 0; q < 2 * r; ++q) {
-    int idx = q < r ? p1[q] : rest[p2[q - r]];
-    for (int d = 0; d < 3; ++d) rep.a2[q * 3 + d] = X[idx * 3 + d];
-    rep.wa2[q] = norm3(&rep.a2[q * 3]);
-  }
-  std::vector<cd> M((size_t)2 * r * r), Qm, Rm;
-  for (int p = 0; p < 2 * r; ++p)
-    for (int q = 0; q < r; ++q) M[(size_t)p * r + q] = rep.wa2[p] * kernel(&rep.a2[p * 3], &rep.b2[q * 3]);
-  thin_qr(M, 2 * r, r, Qm, Rm);
-  rep.Qo = Qm;
-  rep.Ro_inv = tri_inv(Rm, r);
-  for (int p = 0; p < 2 * r; ++p)
-    for (int q = 0; q < r; ++q) M[(size_t)p * r + q] = kernel(&rep.b2[p * 3], &rep.a2[q * 3]) * rep.wa2[q];
-  thin_qr(M, 2 * r, r, Qm, Rm);
-  rep.Qi = Qm;
-  rep.Ri_inv = tri_inv(Rm, r);
-  return rep;
 }
 
-}  // namespace
+Rep build_from_samples(const Samples& sm, const SkelParams& prm) {
+  std::vector<int> piv, p1, p2;
+  std::vector<double> diag;
+  sketch_pivots_host(sm, prm, piv, diag);
+  const int r = rank_from_pivots(diag, (int)piv.size(), prm);
+  const std::vector<double> b = box_points(sm, piv, r);
+  check_pivots_host(sm, b, r, p1, p2);
+  return finish_rep(sm, piv, r, p1, p2);
+}
+
 
 const std::vector<Sym>& symmetries() {
   static std::vector<Sym> syms = [] {
@@ -461,18 +447,82 @@ void canonical_cells(int n, std::vector<int>& canon, std::vector<int>& which) {
   }
 }
 
-Rep build_rep(double w, int cell, double w_top, const SkelParams& prm) {
+Samples make_samples(double w, int cell, double w_top, const SkelParams& prm) {
   int64_t tol = (int64_t)std::llround(-std::log10(prm.eps_op) * 100);
   bool lf = cell < 0;
   uint64_t seed = stream_seed(lf ? 2 : 1, w, lf ? 0 : cell, w_top, tol);
   Stream st(seed);
-  std::vector<double> Y, X((size_t)prm.S_X * 3);
-  box_samples_mixed(st, w, prm.S_Y, Y);
+  Samples sm;
+  sm.w = w;
+  sm.cell = lf ? -1 : cell;
+  sm.SY = prm.S_Y;
+  sm.SX = prm.S_X;
+  sm.X.resize((size_t)prm.S_X * 3);
+  box_samples_mixed(st, w, prm.S_Y, sm.Y);
   for (int q = 0; q < prm.S_X; ++q) {
     P3 p = lf ? lf_point(st, w, w_top) : hf_point(st, w, cell, w_top);
-    for (int d = 0; d < 3; ++d) X[q * 3 + d] = p.x[d];
+    for (int d = 0; d < 3; ++d) sm.X[q * 3 + d] = p.x[d];
   }
-  return build_from_samples(Y, prm.S_Y, X, prm.S_X, prm, splitmix64(seed ^ 0x5DEECE66Dull), w, lf ? -1 : cell);
+  sm.Wx.resize(prm.S_X);
+  for (int i = 0; i < prm.S_X; ++i) sm.Wx[i] = norm3(&sm.X[i * 3]);
+  sm.sketch_seed = splitmix64(seed ^ 0x5DEECE66Dull);
+  return sm;
+}
+
+int rank_from_pivots(const std::vector<double>& diag, int npiv, const SkelParams& prm) {
+  int r = 0;
+  for (double d : diag) if (d > prm.eps_op * diag[0]) ++r;
+  if (2 * r > npiv) throw std::runtime_error("representation rank too large for the sketch");
+  return r;
+}
+
+std::vector<double> box_points(const Samples& sm, const std::vector<int>& piv, int n) {
+  std::vector<double> b((size_t)n * 3);
+  for (int q = 0; q < n; ++q)
+    for (int d = 0; d < 3; ++d) b[q * 3 + d] = sm.Y[piv[q] * 3 + d];
+  return b;
+}
+
+std::vector<int> rest_of(const std::vector<int>& p1, int n) {
+  std::vector<char> used(n, 0);
+  for (int p : p1) used[p] = 1;
+  std::vector<int> rest;
+  for (int i = 0; i < n; ++i) if (!used[i]) rest.push_back(i);
+  return rest;
+}
+
+Rep finish_rep(const Samples& sm, const std::vector<int>& piv, int r, const std::vector<int>& p1,
+               const std::vector<int>& p2) {
+  if ((int)p1.size() != r || (int)p2.size() != r) throw std::runtime_error("check-point selection failed");
+  const std::vector<int> rest = rest_of(p1, sm.SX);
+  Rep rep;
+  rep.w = sm.w;
+  rep.cell = sm.cell;
+  rep.r = r;
+  rep.b2 = box_points(sm, piv, 2 * r);
+  rep.a2.resize((size_t)2 * r * 3);
+  rep.wa2.resize(2 * r);
+  for (int q = 0; q < 2 * r; ++q) {
+    int idx = q < r ? p1[q] : rest[p2[q - r]];
+    for (int d = 0; d < 3; ++d) rep.a2[q * 3 + d] = sm.X[idx * 3 + d];
+    rep.wa2[q] = norm3(&rep.a2[q * 3]);
+  }
+  std::vector<cd> M((size_t)2 * r * r), Qm, Rm;
+  for (int p = 0; p < 2 * r; ++p)
+    for (int q = 0; q < r; ++q) M[(size_t)p * r + q] = rep.wa2[p] * kernel(&rep.a2[p * 3], &rep.b2[q * 3]);
+  thin_qr(M, 2 * r, r, Qm, Rm);
+  rep.Qo = Qm;
+  rep.Ro_inv = tri_inv(Rm, r);
+  for (int p = 0; p < 2 * r; ++p)
+    for (int q = 0; q < r; ++q) M[(size_t)p * r + q] = kernel(&rep.b2[p * 3], &rep.a2[q * 3]) * rep.wa2[q];
+  thin_qr(M, 2 * r, r, Qm, Rm);
+  rep.Qi = Qm;
+  rep.Ri_inv = tri_inv(Rm, r);
+  return rep;
+}
+
+Rep build_rep(double w, int cell, double w_top, const SkelParams& prm) {
+  return build_from_samples(make_samples(w, cell, w_top, prm), prm);
 }
 
 Rep map_rep(const Rep& base, const Sym& s, int cell) {
@@ -487,8 +537,8 @@ Rep map_rep(const Rep& base, const Sym& s, int cell) {
 
 // ------------------------------------------------------------- RepSet ---
 
-RepSet::RepSet(const SkelParams& prm, double w_top, int threads, const std::string& cache_dir)
-    : prm_(prm), w_top_(w_top), threads_(threads), cache_dir_(cache_dir) {}
+RepSet::RepSet(const SkelParams& prm, double w_top, int threads, const std::string& cache_dir, bool on_device)
+    : prm_(prm), w_top_(w_top), threads_(threads), cache_dir_(cache_dir), on_device_(on_device) {}
 
 Rep* RepSet::find(std::vector<std::pair<std::pair<double, int>, Rep>>& v, double w, int cell) {
   for (auto& e : v)
@@ -548,34 +598,81 @@ void RepSet::prepare(const std::vector<std::pair<double, int>>& types) {
     for (auto& x : todo) if (x.first == t.first && x.second == c0) have = true;
     if (!have) todo.push_back({t.first, c0});
   }
-  std::vector<Rep> out(todo.size());
-  std::atomic<size_t> next(0);
-  std::string err;
-  std::mutex mu;
-  auto worker = [&]() {
-    for (;;) {
-      size_t i = next.fetch_add(1);
-      if (i >= todo.size()) return;
-      try {
-        std::string fn;
-        if (!cache_dir_.empty()) {
-          fn = cache_name(cache_dir_, todo[i].first, todo[i].second, w_top_, prm_);
-          if (load_rep(fn, out[i])) continue;
+  const size_t n = todo.size();
+  auto clock = [] { return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count(); };
+  double t0 = clock();
+  std::vector<Rep> out(n);
+  std::vector<char> have(n, 0);
+  std::vector<std::string> fn(n);
+  // fn(i) for i < count on up to threads_ host threads; the first error is rethrown
+  auto parallel = [&](size_t count, const std::function<void(size_t)>& body) {
+    std::atomic<size_t> next(0);
+    std::string err;
+    std::mutex mu;
+    auto worker = [&]() {
+      for (;;) {
+        size_t i = next.fetch_add(1);
+        if (i >= count) return;
+        try {
+          body(i);
+        } catch (const std::exception& e) {
+          std::lock_guard<std::mutex> g(mu);
+          if (err.empty()) err = e.what();
         }
-        out[i] = build_rep(todo[i].first, todo[i].second, w_top_, prm_);
-        if (!fn.empty()) save_rep(fn, out[i]);
-      } catch (const std::exception& e) {
-        std::lock_guard<std::mutex> g(mu);
-        err = e.what();
       }
-    }
+    };
+    int nt = threads_ > 0 ? threads_ : (int)std::thread::hardware_concurrency();
+    nt = std::max(1, std::min<int>(nt, (int)count));
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
+    for (auto& t : pool) t.join();
+    if (!err.empty()) throw std::runtime_error(err);
   };
-  int nt = threads_ > 0 ? threads_ : (int)std::thread::hardware_concurrency();
-  nt = std::max(1, std::min<int>(nt, (int)todo.size()));
-  std::vector<std::thread> pool;
-  for (int t = 0; t < nt; ++t) pool.emplace_back(worker);
-  for (auto& t : pool) t.join();
-  if (!err.empty()) throw std::runtime_error(err);
+  parallel(n, [&](size_t i) {
+    if (cache_dir_.empty()) return;
+    fn[i] = cache_name(cache_dir_, todo[i].first, todo[i].second, w_top_, prm_);
+    if (load_rep(fn[i], out[i])) have[i] = 1;
+  });
+  std::vector<size_t> miss;
+  for (size_t i = 0; i < n; ++i)
+    if (!have[i]) miss.push_back(i);
+  seconds[0] += clock() - t0;
+  t0 = clock();
+  if (!on_device_) {
+    parallel(miss.size(), [&](size_t k) {
+      const size_t i = miss[k];
+      out[i] = build_rep(todo[i].first, todo[i].second, w_top_, prm_);
+      if (!fn[i].empty()) save_rep(fn[i], out[i]);
+    });
+    seconds[1] += clock() - t0;
+  } else if (!miss.empty()) {
+    // samples on the host, both pivot stages on the GPU for all missing types
+    // at once, the least-squares factors on the host again
+    std::vector<Samples> sm(miss.size());
+    parallel(miss.size(), [&](size_t k) { sm[k] = make_samples(todo[miss[k]].first, todo[miss[k]].second, w_top_, prm_); });
+    seconds[0] += clock() - t0;
+    t0 = clock();
+    std::vector<SketchJob> sj(miss.size());
+    for (size_t k = 0; k < miss.size(); ++k) sj[k].sm = &sm[k];
+    sketch_pivots_device(sj, prm_);
+    seconds[1] += clock() - t0;
+    t0 = clock();
+    std::vector<CheckJob> cj(miss.size());
+    for (size_t k = 0; k < miss.size(); ++k) {
+      cj[k].sm = &sm[k];
+      cj[k].r = rank_from_pivots(sj[k].diag, (int)sj[k].piv.size(), prm_);
+      cj[k].b = box_points(sm[k], sj[k].piv, cj[k].r);
+    }
+    check_pivots_device(cj);
+    seconds[2] += clock() - t0;
+    t0 = clock();
+    parallel(miss.size(), [&](size_t k) {
+      const size_t i = miss[k];
+      out[i] = finish_rep(sm[k], sj[k].piv, cj[k].r, cj[k].p1, cj[k].p2);
+      if (!fn[i].empty()) save_rep(fn[i], out[i]);
+    });
+    seconds[3] += clock() - t0;
+  }
   for (size_t i = 0; i < todo.size(); ++i) base_.push_back({todo[i], std::move(out[i])});
 }
 

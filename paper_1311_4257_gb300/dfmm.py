@@ -34,7 +34,7 @@ class Options(ctypes.Structure):
                 ("host_threads", ctypes.c_int32), ("cache_dir", ctypes.c_char_p), ("tc_stages", ctypes.c_int32),
                 ("wait_test", ctypes.c_int32), ("tile_order", ctypes.c_int32), ("p2p_mode", ctypes.c_int32),
                 ("tc_layout", ctypes.c_int32), ("tc_accumulate", ctypes.c_int32), ("tc_precision", ctypes.c_int32),
-                ("arith", ctypes.c_int32)]
+                ("arith", ctypes.c_int32), ("skeleton_host", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -48,7 +48,8 @@ class Stats(ctypes.Structure):
                 ("plan_bytes", ctypes.c_int64), ("plan_seconds", ctypes.c_double), ("m2l_flops", ctypes.c_double),
                 ("other_translation_flops", ctypes.c_double), ("hf_ops", ctypes.c_int64 * 32),
                 ("p2p_close_pairs", ctypes.c_int64), ("arith", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("plan_phase_seconds", ctypes.c_double * 8)]
+                ("plan_phase_seconds", ctypes.c_double * 8), ("skeleton_phase_seconds", ctypes.c_double * 4),
+                ("skeleton_types", ctypes.c_int64)]
 
     def to_dict(self) -> dict:
         n = self.n_levels
@@ -110,6 +111,7 @@ def lib() -> ctypes.CDLL:
         L.dfmm_apply_launches.argtypes = [vp, i32]
         L.dfmm_apply_launches.restype = i64
         L.dfmm_representation.argtypes = [dbl, i32, dbl, dbl, i32, i32, i32, ctypes.POINTER(i32), vp, vp, i32]
+        L.dfmm_representation_device.argtypes = [dbl, i32, dbl, dbl, i32, i32, i32, ctypes.POINTER(i32), vp, vp, i32]
         L.dfmm_plan_bytes.argtypes = [vp]
         L.dfmm_plan_bytes.restype = i64
         L.dfmm_apply_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
@@ -132,7 +134,7 @@ def lib() -> ctypes.CDLL:
         L.dfmm_measure_peaks.argtypes = [ctypes.POINTER(Peaks)]
         L.dfmm_last_error.restype = ctypes.c_char_p
         for f in ("dfmm_plan", "dfmm_apply", "dfmm_apply_host", "dfmm_sync_status", "dfmm_destroy",
-                  "dfmm_plan_stats", "dfmm_export", "dfmm_representation", "dfmm_profile", "dfmm_apply_batched",
+                  "dfmm_plan_stats", "dfmm_export", "dfmm_representation", "dfmm_representation_device", "dfmm_profile", "dfmm_apply_batched",
                   "dfmm_server_create", "dfmm_server_submit", "dfmm_server_wait", "dfmm_server_stats",
                   "dfmm_server_destroy", "dfmm_solve", "dfmm_graph_create", "dfmm_graph_launch",
                   "dfmm_graph_destroy", "dfmm_measure_peaks", "dfmm_batch_create", "dfmm_batch_launch",
@@ -148,14 +150,16 @@ def _check(code: int):
 
 
 def representation(w: float, cell: int, w_top: float, eps_op: float, sample_box: int = 0, sample_far: int = 0,
-                   sketch_rows: int = 0):
-    """Host-only: (rank, b2 [2r,3], a2 [2r,3]) of one representation type."""
+                   sketch_rows: int = 0, device: bool = False):
+    """(rank, b2 [2r,3], a2 [2r,3]) of one representation type; pivot selection on
+    host threads, or on the current GPU with device=True."""
     r = ctypes.c_int(0)
     cap = 1024
     b2 = np.zeros((cap, 3))
     a2 = np.zeros((cap, 3))
-    _check(lib().dfmm_representation(w, cell, w_top, eps_op, sample_box, sample_far, sketch_rows,
-                                      ctypes.byref(r), b2.ctypes.data, a2.ctypes.data, cap))
+    fn = lib().dfmm_representation_device if device else lib().dfmm_representation
+    _check(fn(w, cell, w_top, eps_op, sample_box, sample_far, sketch_rows,
+              ctypes.byref(r), b2.ctypes.data, a2.ctypes.data, cap))
     n = 2 * r.value
     return r.value, b2[:n].copy(), a2[:n].copy()
 
@@ -181,7 +185,7 @@ class Plan:
                  sketch_rows: int = 0, eps_op_factor: float = 0.0, host_threads: int = 0,
                  cache_dir: str | None = None, m2l_mode: int = 0, tc_stages: int = 0, wait_test: int = 0,
                  tile_order: int = 0, p2p_mode: int = 0, tc_layout: int = 0,
-                 tc_accumulate: int = 0, tc_precision: int = 0, arith: int = 0):
+                 tc_accumulate: int = 0, tc_precision: int = 0, arith: int = 0, skeleton_host: int = 0):
         import torch
         if not (isinstance(points, torch.Tensor) and points.is_cuda):
             points = torch.as_tensor(np.ascontiguousarray(points, dtype=np.float64), device="cuda")
@@ -193,7 +197,7 @@ class Plan:
         self.eps = float(eps)
         o = Options(leaf_max, sample_box, sample_far, sketch_rows, eps_op_factor, m2l_mode, host_threads,
                     cache_dir.encode() if cache_dir else None, tc_stages, wait_test, tile_order, p2p_mode, tc_layout, tc_accumulate, tc_precision,
-                    arith)
+                    arith, skeleton_host)
         h = ctypes.c_void_p()
         _check(lib().dfmm_plan(points.data_ptr(), self.N, self.K, self.eps, ctypes.byref(o), ctypes.byref(h)))
         self._h = h

@@ -47,7 +47,11 @@ def _apply(plan, f):
 def sphere4():
     from paper_1311_4257_gb300 import Plan
     p = workloads.sphere(4.0, 0)
-    g = Plan(p, 4.0, 1e-8)
+    # host pivot selection: its skeletons are the oracle's, so the FMM-vs-FMM
+    # comparison below sees only rounding.  At eps_op = 1e-9 the GPU selection
+    # may pick other, equally valid, near-tied pivots (reading A15);
+    # test_sphere_k8_eps1e8_all_targets runs the default GPU selection.
+    g = Plan(p, 4.0, 1e-8, skeleton_host=1)
     return p, g
 
 
