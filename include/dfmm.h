@@ -48,7 +48,8 @@ typedef enum {
   DFMM_ERR_CUDA = -4,         /* a CUDA runtime / cuBLAS call failed */
   DFMM_ERR_UNSUPPORTED = -5,  /* eps outside [1e-8, 1e-2], K outside (0, 4096] */
   DFMM_ERR_TIMEOUT = -6,      /* a device-side bounded wait gave up */
-  DFMM_ERR_DEVICE = -7        /* a device-side check failed (status word set) */
+  DFMM_ERR_DEVICE = -7,       /* a device-side check failed (status word set) */
+  DFMM_ERR_CANCELLED = -8     /* a queued server request was cancelled (dfmm_server_cancel) */
 } dfmm_status;
 
 /* Plan-time options.  Zero-initialise and set what you need; zero fields take
@@ -151,7 +152,25 @@ int dfmm_apply_host(dfmm_plan_t plan, const void* f_host, void* u_host, int nrhs
  * `stream`.  Returns DFMM_OK, DFMM_ERR_TIMEOUT or DFMM_ERR_DEVICE. */
 int dfmm_sync_status(dfmm_plan_t plan, cudaStream_t stream);
 
-/* Free every resource of the plan (waits for the device first). */
+/* Device-side bounds check of every index table of the plan: translation
+ * pairs against the rows of their source and target states, the work tiles of
+ * every workspace laid out so far against operator and pair counts, the
+ * per-point row maps and leaf jobs, the W- and X-list jobs, the near-field
+ * leaves, offsets, sources and staging list, the close pairs and the
+ * permutation.  The check kernels only read the tables.  Returns DFMM_OK, or
+ * DFMM_ERR_DEVICE naming the first table with an entry out of range
+ * (dfmm_last_error).  Synchronises `stream`.  A library built with
+ * DFMM_CHECK=1 (paper_1311_4257_gb300/build.py) runs it at the end of every
+ * dfmm_plan.
+ *   flags: 0, or DFMM_VALIDATE_PLANT (testing aid): also check a scratch copy
+ *          of one translation pair table whose first source row is set to
+ *          its bound; the plan is not touched, and the call must fail. */
+#define DFMM_VALIDATE_PLANT 1
+int dfmm_validate(dfmm_plan_t plan, cudaStream_t stream, int flags);
+
+/* Free every resource of the plan (waits for the device first).  NULL is a
+ * no-op; a handle that is not a live plan, or a plan that a request server
+ * still holds (queued or running requests), is refused with DFMM_ERR_INVALID. */
 int dfmm_destroy(dfmm_plan_t plan);
 
 /* Sizes and counts of a plan, for reports and tests. */
@@ -359,6 +378,18 @@ int dfmm_solve(dfmm_plan_t plan, double alpha_re, double alpha_im, double beta_r
  * have passed (DFMM_ERR_TIMEOUT; the ticket stays valid), then returns the
  * request's status and, if latency_ms is not NULL, its submit-to-finish time.
  * A ticket can be collected once.
+ * dfmm_server_cancel removes a request that has not started from the queue:
+ * its wait returns DFMM_ERR_CANCELLED and u_host is not written.  A request
+ * that has started or finished is not cancelled (DFMM_ERR_INVALID); it
+ * completes normally.
+ * dfmm_server_fail_next (testing aid for the failure path): the next group
+ * the dispatcher starts fails on the host before anything is queued for it,
+ * as a failed staging copy would; its requests finish with `status` (a
+ * negative dfmm_status) and the server goes on with the others.
+ * A submitted request holds its plan: dfmm_server_submit refuses a handle that
+ * is not a live plan (never created, or destroyed: DFMM_ERR_INVALID), and
+ * dfmm_destroy refuses a plan while requests on it are queued or running.
+ * Cancelled and failed requests count in requests_failed.
  * dfmm_server_destroy finishes every queued request, then frees the server. */
 typedef struct dfmm_server_s* dfmm_server_t;
 
@@ -380,6 +411,8 @@ int dfmm_server_create(int streams, int64_t budget_bytes, int max_rhs, dfmm_serv
 int dfmm_server_submit(dfmm_server_t server, dfmm_plan_t plan, const void* f_host, void* u_host, int nrhs,
                        int64_t* ticket);
 int dfmm_server_wait(dfmm_server_t server, int64_t ticket, double timeout_seconds, double* latency_ms);
+int dfmm_server_cancel(dfmm_server_t server, int64_t ticket);
+int dfmm_server_fail_next(dfmm_server_t server, int status);
 int dfmm_server_stats(dfmm_server_t server, dfmm_server_report* out);
 int dfmm_server_destroy(dfmm_server_t server);
 

@@ -15,7 +15,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdfmm.so")
 
-SOURCES = ["sort.cu", "tree.cu", "operators.cu", "apply.cu", "apply64.cu", "skeleton_gpu.cu", "m2l_tc.cu", "m2l_cx.cu", "noalloc.cu", "probes.cu", "skeleton.cpp", "dfmm.cpp",
+SOURCES = ["sort.cu", "tree.cu", "operators.cu", "apply.cu", "apply64.cu", "skeleton_gpu.cu", "validate.cu", "m2l_tc.cu", "m2l_cx.cu", "noalloc.cu", "probes.cu", "skeleton.cpp", "dfmm.cpp",
            "serve.cpp", "solve.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -29,6 +29,8 @@ def nvcc() -> str:
 
 def _flags(src: str) -> list[str]:
     f = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+    if os.environ.get("DFMM_CHECK") == "1":   # bounds-checking build: dfmm_plan validates every plan
+        f += ["-DDFMM_CHECK"]
     if src.endswith(".cu"):
         f += ARCH + ["--expt-relaxed-constexpr", "-Xptxas", "-v"] if os.environ.get("DFMM_PTXAS_V") else ARCH
         if src == "apply.cu":
@@ -48,7 +50,7 @@ def build(verbose: bool = False) -> str:
     objs = []
     cmds = []
     for s in srcs:
-        o = os.path.join(BUILD, s + ".o")
+        o = os.path.join(BUILD, s + (".check" if os.environ.get("DFMM_CHECK") == "1" else "") + ".o")
         objs.append(o)
         src = os.path.join(CSRC, s)
         deps = [src] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".h")]
@@ -65,7 +67,7 @@ def build(verbose: bool = False) -> str:
                 errs.append(cmd[2])
     if errs:
         raise RuntimeError("nvcc failed for: " + ", ".join(errs))
-    if cmds or not os.path.exists(LIB):
+    if cmds or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         link = [nvcc(), "-shared", "-o", LIB] + objs + ARCH + ["-lcublas", "-lcudart"]
         res = subprocess.run(link, capture_output=True, text=True)
         if res.returncode != 0:

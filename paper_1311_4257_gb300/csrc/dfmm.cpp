@@ -30,6 +30,7 @@
 #include "internal.h"
 #include "operators.h"
 #include "skeleton.h"
+#include "validate.h"
 #include "tree.h"
 
 using namespace dfmm;
@@ -42,6 +43,12 @@ int fail(int code, const std::string& msg) {
   g_err = msg;
   return code;
 }
+
+// Live plans and the number of server requests that hold each one: a handle
+// that is not in the map is not a plan (never created, or destroyed), and a
+// plan with holders is not destroyed.
+std::mutex g_plans_mu;
+std::unordered_map<const void*, int64_t> g_plans;
 
 struct GemmPlan {
   int M = 0, Kd = 0, nops = 0;
@@ -57,6 +64,8 @@ struct GemmPlan {
   double flops_rhs = 0;            // algorithmic flops per right-hand side
   double bytes_fixed = 0;          // operators (bytes once per launch)
   double bytes_rhs = 0;            // unique source rows + target rows (read and write), per rhs
+  int64_t src_rows = 0;            // rows of the source buffer (pair .x < src_rows), for dfmm_validate
+  int64_t dst_rows = 0;            // rows of the target buffer (pair .y < dst_rows)
 };
 
 enum Fam { F_M2L_HF, F_M2L_LF, F_M2M, F_L2L, F_P2L_PROJ, F_P2M_EVAL, F_P2L_EVAL, F_L2P, F_M2P, F_P2P,
@@ -196,6 +205,7 @@ struct dfmm_plan_s {
   int4* p2p_src = nullptr;
   float4* p2p_shift = nullptr;
   uint32_t* p2p_flat = nullptr;   // FP32 near field: flat staging list
+  int64_t n_flat = 0;
   int32_t* close_off = nullptr;   // FP32 near field: close-pair corrections (CSR per sorted point)
   int32_t* close_j = nullptr;
   float2* close_w = nullptr;
@@ -620,6 +630,8 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
       F.p2l_shifts = upload(xs, ar, s);
       F.p2l.fam = F_P2L_PROJ;
       F.p2l.flops_rhs = 8.0 * rp.r * 2 * rp.r * F.n_p2l;
+      F.p2l.src_rows = F.n_p2l;
+      F.p2l.dst_rows = LV[l].n;
       finish_gemm(F.p2l, op, pr, ar, s);
     }
     // LF-M2L over the V list: one operator per offset
@@ -650,6 +662,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
       }
       F.v.fam = F_M2L_LF;
       F.v.flops_rhs = 8.0 * rp.r * rp.r * V.n;
+      F.v.src_rows = F.v.dst_rows = LV[l].n;
       finish_gemm(F.v, op, pr, ar, s);
       m2l_flops += 8.0 * rp.r * rp.r * V.n;
     }
@@ -677,6 +690,8 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
       }
       F.m2m.fam = F_M2M;
       F.m2m.flops_rhs = 8.0 * rp.r * P->lf[l + 1].r * Lc.n;
+      F.m2m.src_rows = Lc.n;
+      F.m2m.dst_rows = LV[l].n;
       finish_gemm(F.m2m, op, pr, ar, s);
       other_flops += F.m2m.flops_rhs;
     }
@@ -701,6 +716,8 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
       }
       F.l2l.fam = F_L2L;
       F.l2l.flops_rhs = 8.0 * rp.r * P->lf[l - 1].r * LV[l].n;
+      F.l2l.src_rows = LV[l - 1].n;
+      F.l2l.dst_rows = LV[l].n;
       finish_gemm(F.l2l, op, pr, ar, s);
       other_flops += F.l2l.flops_rhs;
       (void)Lp;
@@ -767,6 +784,8 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
           H.m2l.ops = ar.alloc<float2>(((size_t)specs.size() * R * R) * P->cw);
           form_ops(kOpM2L, specs, dreps, R, R, H.m2l.ops, P->fp64, cb, ar, s);
         }
+        H.m2l.src_rows = (int64_t)H.out_keys.size();
+        H.m2l.dst_rows = (int64_t)H.in_keys.size();
         finish_gemm(H.m2l, op, pr, ar, s);
       }
       // HF-M2M into this level from its children (level l+1: HF or, at w = 1, LF)
@@ -807,6 +826,8 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
           }
         }
         H.m2m.fam = F_M2M;
+        H.m2m.src_rows = l == P->l1 ? LV[l + 1].n : (int64_t)P->hf[l + 1].out_keys.size();
+        H.m2m.dst_rows = (int64_t)H.out_keys.size();
         finish_gemm(H.m2m, op, pr, ar, s);
         other_flops += H.m2m.flops_rhs;
       }
@@ -842,6 +863,8 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
           }
         }
         H.l2l.fam = F_L2L;
+        H.l2l.src_rows = (int64_t)P->hf[l - 1].in_keys.size();
+        H.l2l.dst_rows = (int64_t)H.in_keys.size();
         finish_gemm(H.l2l, op, pr, ar, s);
         other_flops += H.l2l.flops_rhs;
       }
@@ -880,6 +903,8 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
         }
       }
       F.l2l.fam = F_L2L;
+      F.l2l.src_rows = (int64_t)Hp.in_keys.size();
+      F.l2l.dst_rows = LV[l].n;
       finish_gemm(F.l2l, op, pr, ar, s);
       other_flops += F.l2l.flops_rhs;
     }
@@ -1023,7 +1048,10 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
     P->p2p_src = upload(src, ar, s);
     P->p2p_shift = upload(shifts, ar, s);
     if (P->opt.p2p_mode == 2 && !flat_ok) P->opt.p2p_mode = 1;   // beyond the packed list: double-float form
-    if (P->opt.p2p_mode == 2) P->p2p_flat = upload(flat, ar, s);
+    if (P->opt.p2p_mode == 2) {
+      P->p2p_flat = upload(flat, ar, s);
+      P->n_flat = (int64_t)flat.size();
+    }
     P->stats.p2p_interactions = inter;
     // FP32 form of the near field: its close pairs and their exact corrections
     // (the pairs closer than delta = 1e-6 / eps, at most 0.5; the FP32
@@ -1610,6 +1638,119 @@ void build_images(dfmm_plan_s* P, cudaStream_t s) {
   P->stats.plan_bytes = (int64_t)P->ar.bytes() + (P->close_keep ? (int64_t)P->close_keep->bytes() : 0);
 }
 
+// Bounds checks of every index table of the plan and of the work tiles of
+// every workspace laid out so far (dfmm_validate); names[k] names check k.
+void plan_checks(dfmm_plan_s* P, std::vector<RangeCheck>& c, std::vector<std::string>& names) {
+  const int64_t N = P->N;
+  auto fields = [&](const std::string& nm, const void* p, int64_t n, int stride, int a, int64_t hi_a, int b = -1,
+                    int64_t hi_ab = 0) {
+    RangeCheck r;
+    r.p = p;
+    r.n = n;
+    r.mode = kCheckFields;
+    r.stride = stride;
+    r.a = a;
+    r.b = b;
+    r.hi_a = hi_a;
+    r.hi_ab = hi_ab;
+    c.push_back(r);
+    names.push_back(nm);
+  };
+  auto csr = [&](const std::string& nm, const void* p, int64_t n, bool i64, int64_t total) {
+    RangeCheck r;
+    r.p = p;
+    r.n = n;
+    r.mode = i64 ? kCheckCsr64 : kCheckCsr32;
+    r.hi_a = total;
+    c.push_back(r);
+    names.push_back(nm);
+  };
+  fields("permutation", P->perm, N, 1, 0, N);
+  std::lock_guard<std::mutex> g(P->ws_mu);
+  int si = 0;
+  for (const GemmPlan* gp : all_gemms(P)) {
+    const std::string tag = std::string(kFamName[gp->fam]) + " stage " + std::to_string(si++);
+    if (gp->npairs == 0) continue;
+    fields(tag + " pair sources", gp->pairs, gp->npairs, 2, 0, gp->src_rows);
+    fields(tag + " pair targets", gp->pairs, gp->npairs, 2, 1, gp->dst_rows);
+    for (auto& ws : P->ws)
+      for (auto& t : ws.second->tiles)
+        if (t.first.first == (const void*)gp) {
+          fields(tag + " tile operators", t.second.first, t.second.second, 4, 0, gp->nops);
+          fields(tag + " tile pair ranges", t.second.first, t.second.second, 4, 1, gp->npairs, 2, gp->npairs);
+        }
+  }
+  for (int l = P->l_lf0; l < P->nl; ++l) {
+    const LFLevel& F = P->lf[l];
+    const std::string tag = "level " + std::to_string(l);
+    fields(tag + " L2P rows: points", F.l2p_map, F.n_l2p_rows, 2, 0, N);
+    fields(tag + " L2P rows: boxes", F.l2p_map, F.n_l2p_rows, 2, 1, F.nbox);
+    fields(tag + " leaf jobs: points", F.l2p_jobs, F.n_l2p, 4, 0, N, 1, N);
+    fields(tag + " leaf jobs: rows", F.l2p_jobs, F.n_l2p, 4, 2, F.n_l2p_rows + 1, 1, F.n_l2p_rows);
+    fields(tag + " leaf jobs: boxes", F.l2p_jobs, F.n_l2p, 4, 3, F.nbox);
+    fields(tag + " X-list jobs: points", F.p2l_jobs, F.n_p2l, 4, 0, N, 1, N);
+    fields(tag + " X-list jobs: rows", F.p2l_jobs, F.n_p2l, 4, 2, F.n_p2l);
+    fields(tag + " X-list jobs: shifts", F.p2l_jobs, F.n_p2l, 4, 3, F.n_p2l);
+  }
+  for (size_t k = 0; k < P->m2p.size(); ++k) {
+    const M2PGroup& m = P->m2p[k];
+    const std::string tag = "W-list group " + std::to_string(k);
+    fields(tag + ": points", m.jobs, m.njobs, 4, 0, N, 1, N);
+    fields(tag + ": rows", m.jobs, m.njobs, 4, 2, m.nrows + 1, 1, m.nrows);
+    fields(tag + ": states", m.jobs, m.njobs, 4, 3, P->lf[m.src_level].nbox);
+  }
+  int64_t n_src = 0;
+  DFMM_CUDA(cudaMemcpy(&n_src, P->p2p_off + P->n_leaves, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  fields("near-field leaves", P->p2p_range, P->n_leaves, 2, 0, N, 1, N);
+  csr("near-field list offsets", P->p2p_off, P->n_leaves, true, n_src);
+  fields("near-field sources", P->p2p_src, n_src, 4, 0, N, 1, N);
+  if (P->p2p_flat) {
+    RangeCheck r;
+    r.p = P->p2p_flat;
+    r.n = P->n_flat;
+    r.mode = kCheckPacked;
+    r.hi_a = N;
+    c.push_back(r);
+    names.push_back("near-field staging list");
+  }
+  if (P->close_off) {
+    csr("close-pair offsets", P->close_off, N, false, P->n_close);
+    fields("close-pair sources", P->close_j, P->n_close, 1, 0, N);
+  }
+}
+
+// The checks of plan_checks on `s`; with plant, also a scratch copy of the first
+// non-empty pair table with the source row of its first pair set to its bound.
+// Throws DFMM_ERR_DEVICE naming the first table with an entry out of range.
+void validate_plan(dfmm_plan_s* P, cudaStream_t s, bool plant) {
+  std::vector<RangeCheck> c;
+  std::vector<std::string> names;
+  plan_checks(P, c, names);
+  DevArena ar;
+  if (plant) {
+    for (const GemmPlan* gp : all_gemms(P)) {
+      if (gp->npairs == 0) continue;
+      int2* copy = ar.alloc<int2>(gp->npairs);
+      DFMM_CUDA(cudaMemcpyAsync(copy, gp->pairs, gp->npairs * sizeof(int2), cudaMemcpyDeviceToDevice, s));
+      const int bad = (int)gp->src_rows;
+      DFMM_CUDA(cudaMemcpyAsync(copy, &bad, sizeof(int), cudaMemcpyHostToDevice, s));
+      RangeCheck r;
+      r.p = copy;
+      r.n = gp->npairs;
+      r.stride = 2;
+      r.a = 0;
+      r.hi_a = gp->src_rows;
+      c.push_back(r);
+      names.push_back("planted copy of a pair table");
+      break;
+    }
+  }
+  const std::vector<int64_t> bad = run_range_checks(c, s);
+  for (size_t k = 0; k < c.size(); ++k)
+    if (bad[k] >= 0)
+      throw Error(DFMM_ERR_DEVICE, names[k] + ": entry " + std::to_string(bad[k]) + " out of range");
+}
+
 template <class F>
 int guarded(F&& fn) {
   try {
@@ -1628,6 +1769,20 @@ int guarded(F&& fn) {
 namespace dfmm {
 
 int set_error(int code, const char* msg) { return fail(code, msg); }
+
+bool plan_acquire(const dfmm_plan_s* plan) {
+  std::lock_guard<std::mutex> g(g_plans_mu);
+  auto it = g_plans.find(plan);
+  if (it == g_plans.end()) return false;
+  ++it->second;
+  return true;
+}
+
+void plan_release(const dfmm_plan_s* plan) {
+  std::lock_guard<std::mutex> g(g_plans_mu);
+  auto it = g_plans.find(plan);
+  if (it != g_plans.end() && it->second > 0) --it->second;
+}
 
 int apply_with_scratch(dfmm_plan_s* P, const void* f, void* u, int nrhs, cudaStream_t stream, void* scratch,
                        size_t bytes) {
@@ -1944,6 +2099,13 @@ int dfmm_plan(const double* points, int64_t N, double K, double eps, const dfmm_
       P->stats.plan_seconds += P->stats.plan_phase_seconds[6];
     }
     DFMM_CUDA(cudaStreamSynchronize(s));
+#ifdef DFMM_CHECK
+    validate_plan(P.get(), s, false);   // the bounds-checking build checks every plan it makes
+#endif
+    {
+      std::lock_guard<std::mutex> g(g_plans_mu);
+      g_plans[P.get()] = 0;
+    }
     *out = P.release();
     return DFMM_OK;
   });
@@ -1996,9 +2158,25 @@ int dfmm_sync_status(dfmm_plan_t plan, cudaStream_t stream) {
   });
 }
 
+int dfmm_validate(dfmm_plan_t plan, cudaStream_t stream, int flags) {
+  return guarded([&]() -> int {
+    if (!plan) return fail(DFMM_ERR_INVALID, "null plan");
+    if (flags & ~DFMM_VALIDATE_PLANT) return fail(DFMM_ERR_INVALID, "unknown flags");
+    validate_plan(plan, stream, (flags & DFMM_VALIDATE_PLANT) != 0);
+    return DFMM_OK;
+  });
+}
+
 int dfmm_destroy(dfmm_plan_t plan) {
   return guarded([&]() -> int {
     if (!plan) return DFMM_OK;
+    {
+      std::lock_guard<std::mutex> g(g_plans_mu);
+      auto it = g_plans.find(plan);
+      if (it == g_plans.end()) return fail(DFMM_ERR_INVALID, "not a live plan");
+      if (it->second > 0) return fail(DFMM_ERR_INVALID, "the plan has requests queued or running in a server");
+      g_plans.erase(it);
+    }
     cudaDeviceSynchronize();
     delete plan;
     return DFMM_OK;

@@ -10,6 +10,12 @@ namespace dfmm {
 // Records `msg` as the calling thread's last error and returns `code`.
 int set_error(int code, const char* msg);
 
+// Server requests hold their plan: plan_acquire returns false for a handle that
+// is not a live plan, else counts one holder (dfmm_destroy refuses a plan with
+// holders); plan_release drops one.
+bool plan_acquire(const dfmm_plan_s* plan);
+void plan_release(const dfmm_plan_s* plan);
+
 // The matvec of dfmm_apply with every per-apply buffer (states, staging
 // buffers, work tiles) laid out inside the caller-provided device memory
 // [scratch, scratch + bytes); no device memory is allocated.

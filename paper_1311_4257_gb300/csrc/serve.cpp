@@ -119,6 +119,7 @@ struct dfmm_server_s {
   std::unordered_map<int64_t, std::shared_ptr<Request>> live;   // submitted, not yet collected
   int64_t next_ticket = 1;
   bool stop = false;
+  int fail_next = 0;                    // testing aid: status the next group fails with (0 = none)
   std::thread worker;
   std::map<std::pair<dfmm_plan_t, int>, size_t> ws_bytes;    // workspace bytes per (plan, nrhs)
   // statistics
@@ -144,6 +145,7 @@ struct dfmm_server_s {
     for (auto& r : sl.group) {
       r->t_done = t;
       r->status = status;
+      dfmm::plan_release(r->plan);
       if (status == DFMM_OK) {
         ++n_done;
         rhs_done += r->nrhs;
@@ -168,7 +170,7 @@ struct dfmm_server_s {
   // Starts a group on a free slot (mu not held).  Copies the densities in,
   // runs the apply inside the group's arena range, copies the results out and
   // queues the completion callback.
-  void launch(Slot& sl, int total_rhs) {
+  void launch(Slot& sl, int total_rhs, int injected) {
     dfmm_plan_t plan = sl.group.front()->plan;
     dfmm_stats st{};
     dfmm_plan_stats(plan, &st);
@@ -179,9 +181,10 @@ struct dfmm_server_s {
     char* u_dev = p + align256(N * total_rhs * eb);
     char* scratch = p + 2 * align256(N * total_rhs * eb);
     const size_t scratch_bytes = sl.bytes - 2 * align256(N * total_rhs * eb);
-    int rc = DFMM_OK;
+    int rc = injected;   // a failure injected on the host: nothing is queued for this group
     size_t k = 0;
     for (auto& r : sl.group) {
+      if (rc != DFMM_OK) break;
       if (cudaMemcpyAsync(f_dev + k * N * eb, r->f_host, N * r->nrhs * eb, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
         rc = DFMM_ERR_CUDA;
       k += r->nrhs;
@@ -229,6 +232,7 @@ struct dfmm_server_s {
           pending.pop_front();
           r->status = DFMM_ERR_OOM;
           r->t_done = now_s();
+          dfmm::plan_release(r->plan);
           ++n_failed;
           cv_done.notify_all();
           progressed = true;
@@ -242,8 +246,16 @@ struct dfmm_server_s {
         sl->off = (size_t)off;
         sl->bytes = need;
         max_running = std::max(max_running, ++running);
+        const int injected = fail_next;
+        fail_next = 0;
         lk.unlock();
-        launch(*sl, total);
+        try {
+          launch(*sl, total, injected);
+        } catch (...) {   // a host-side failure while queueing: the group fails, the server goes on
+          cudaStreamSynchronize(sl->stream);
+          std::lock_guard<std::mutex> g(mu);
+          if (sl->busy) finish(*sl, DFMM_ERR_INVALID);
+        }
         lk.lock();
         progressed = true;
       }
@@ -302,6 +314,7 @@ int dfmm_server_create(int streams, int64_t budget_bytes, int max_rhs, dfmm_serv
 int dfmm_server_submit(dfmm_server_t s, dfmm_plan_t plan, const void* f_host, void* u_host, int nrhs, int64_t* ticket) {
   if (!s || !plan || !f_host || !u_host || !ticket) return serr(DFMM_ERR_INVALID, "null argument");
   if (nrhs < 1 || nrhs > 64) return serr(DFMM_ERR_INVALID, "nrhs must be in [1, 64]");
+  if (!dfmm::plan_acquire(plan)) return serr(DFMM_ERR_INVALID, "not a live plan (never created, or destroyed)");
   auto r = std::make_shared<Request>();
   r->plan = plan;
   r->f_host = f_host;
@@ -310,7 +323,10 @@ int dfmm_server_submit(dfmm_server_t s, dfmm_plan_t plan, const void* f_host, vo
   r->t_submit = now_s();
   {
     std::lock_guard<std::mutex> g(s->mu);
-    if (s->stop) return serr(DFMM_ERR_INVALID, "the server is shutting down");
+    if (s->stop) {
+      dfmm::plan_release(plan);
+      return serr(DFMM_ERR_INVALID, "the server is shutting down");
+    }
     r->ticket = s->next_ticket++;
     if (s->t_first_submit == 0) s->t_first_submit = r->t_submit;
     s->pending.push_back(r);
@@ -335,8 +351,36 @@ int dfmm_server_wait(dfmm_server_t s, int64_t ticket, double timeout_seconds, do
   s->live.erase(ticket);
   if (latency_ms) *latency_ms = 1e3 * (r->t_done - r->t_submit);
   if (r->status != DFMM_OK)
-    return serr(r->status, r->status == DFMM_ERR_OOM ? "the request does not fit in the server's memory budget"
-                                                     : "the request's apply failed");
+    return serr(r->status, r->status == DFMM_ERR_OOM         ? "the request does not fit in the server's memory budget"
+                           : r->status == DFMM_ERR_CANCELLED ? "the request was cancelled"
+                                                             : "the request's apply failed");
+  return DFMM_OK;
+}
+
+int dfmm_server_cancel(dfmm_server_t s, int64_t ticket) {
+  if (!s) return serr(DFMM_ERR_INVALID, "null server");
+  std::lock_guard<std::mutex> g(s->mu);
+  auto it = s->live.find(ticket);
+  if (it == s->live.end()) return serr(DFMM_ERR_INVALID, "unknown or already collected ticket");
+  auto q = std::find(s->pending.begin(), s->pending.end(), it->second);
+  if (q == s->pending.end())
+    return serr(DFMM_ERR_INVALID, it->second->status == 1 ? "the request has started; it will complete"
+                                                          : "the request has finished");
+  std::shared_ptr<Request> r = *q;
+  s->pending.erase(q);
+  r->status = DFMM_ERR_CANCELLED;
+  r->t_done = now_s();
+  dfmm::plan_release(r->plan);
+  ++s->n_failed;
+  s->cv_done.notify_all();
+  return DFMM_OK;
+}
+
+int dfmm_server_fail_next(dfmm_server_t s, int status) {
+  if (!s) return serr(DFMM_ERR_INVALID, "null server");
+  if (status >= 0) return serr(DFMM_ERR_INVALID, "status must be a negative dfmm_status");
+  std::lock_guard<std::mutex> g(s->mu);
+  s->fail_next = status;
   return DFMM_OK;
 }
 

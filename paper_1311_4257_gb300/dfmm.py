@@ -16,6 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdfmm.so")
 
 OK, ERR_INVALID, ERR_DOMAIN, ERR_OOM, ERR_CUDA, ERR_UNSUPPORTED, ERR_TIMEOUT, ERR_DEVICE = 0, -1, -2, -3, -4, -5, -6, -7
+ERR_CANCELLED = -8
 
 EXPORT = {"perm": 0, "keys": 1, "boxes": 2, "hf_pairs": 3, "slots_out": 4, "slots_in": 5, "v_pairs": 6,
           "u_pairs": 7, "w_pairs": 8, "x_pairs": 9, "ranks": 10}
@@ -102,6 +103,7 @@ def lib() -> ctypes.CDLL:
         L.dfmm_apply.argtypes = [vp, vp, vp, i32, vp]
         L.dfmm_apply_host.argtypes = [vp, vp, vp, i32, vp]
         L.dfmm_sync_status.argtypes = [vp, vp]
+        L.dfmm_validate.argtypes = [vp, vp, i32]
         L.dfmm_destroy.argtypes = [vp]
         L.dfmm_plan_stats.argtypes = [vp, ctypes.POINTER(Stats)]
         L.dfmm_apply_workspace_bytes.argtypes = [vp, i32]
@@ -119,6 +121,8 @@ def lib() -> ctypes.CDLL:
         L.dfmm_server_create.argtypes = [i32, i64, i32, ctypes.POINTER(vp)]
         L.dfmm_server_submit.argtypes = [vp, vp, vp, vp, i32, ctypes.POINTER(i64)]
         L.dfmm_server_wait.argtypes = [vp, i64, dbl, ctypes.POINTER(dbl)]
+        L.dfmm_server_cancel.argtypes = [vp, i64]
+        L.dfmm_server_fail_next.argtypes = [vp, i32]
         L.dfmm_server_stats.argtypes = [vp, ctypes.POINTER(ServerReport)]
         L.dfmm_server_destroy.argtypes = [vp]
         L.dfmm_graph_create.argtypes = [vp, vp, vp, i32, vp, ctypes.POINTER(vp)]
@@ -133,9 +137,10 @@ def lib() -> ctypes.CDLL:
                                  ctypes.POINTER(dbl)]
         L.dfmm_measure_peaks.argtypes = [ctypes.POINTER(Peaks)]
         L.dfmm_last_error.restype = ctypes.c_char_p
-        for f in ("dfmm_plan", "dfmm_apply", "dfmm_apply_host", "dfmm_sync_status", "dfmm_destroy",
+        for f in ("dfmm_plan", "dfmm_apply", "dfmm_apply_host", "dfmm_sync_status", "dfmm_validate", "dfmm_destroy",
                   "dfmm_plan_stats", "dfmm_export", "dfmm_representation", "dfmm_representation_device", "dfmm_profile", "dfmm_apply_batched",
-                  "dfmm_server_create", "dfmm_server_submit", "dfmm_server_wait", "dfmm_server_stats",
+                  "dfmm_server_create", "dfmm_server_submit", "dfmm_server_wait", "dfmm_server_cancel",
+                  "dfmm_server_fail_next", "dfmm_server_stats",
                   "dfmm_server_destroy", "dfmm_solve", "dfmm_graph_create", "dfmm_graph_launch",
                   "dfmm_graph_destroy", "dfmm_measure_peaks", "dfmm_batch_create", "dfmm_batch_launch",
                   "dfmm_batch_stats", "dfmm_batch_destroy"):
@@ -253,6 +258,10 @@ class Plan:
     def sync_status(self, stream=None) -> int:
         return lib().dfmm_sync_status(self._h, _stream_ptr(stream))
 
+    def validate(self, plant: bool = False, stream=None):
+        """dfmm_validate: device-side bounds check of every index table (raises DfmmError)."""
+        _check(lib().dfmm_validate(self._h, _stream_ptr(stream), 1 if plant else 0))
+
     def stats(self) -> dict:
         s = Stats()
         _check(lib().dfmm_plan_stats(self._h, ctypes.byref(s)))
@@ -302,8 +311,9 @@ class Plan:
         return buf[:n.value].reshape(-1, EXPORT_COLS[wid])
 
     def close(self):
+        """dfmm_destroy; refused (DfmmError) while a request server holds the plan."""
         if getattr(self, "_h", None):
-            lib().dfmm_destroy(self._h)
+            _check(lib().dfmm_destroy(self._h))
             self._h = None
 
     def __del__(self):
@@ -430,6 +440,14 @@ class Server:
         lat = ctypes.c_double(0)
         _check(lib().dfmm_server_wait(self._h, ticket, timeout, ctypes.byref(lat)))
         return lat.value
+
+    def cancel(self, ticket: int):
+        """dfmm_server_cancel: drop a request that has not started."""
+        _check(lib().dfmm_server_cancel(self._h, ticket))
+
+    def fail_next(self, status: int):
+        """dfmm_server_fail_next (testing aid): the next group fails on the host with `status`."""
+        _check(lib().dfmm_server_fail_next(self._h, status))
 
     def stats(self) -> dict:
         r = ServerReport()

@@ -74,3 +74,36 @@ def test_status_is_ok_after_ordinary_applies(env):
         plan = dfmm.Plan(p, 4.0, 1e-5, m2l_mode=mode)
         plan.apply(fd)
         assert plan.sync_status() == dfmm.OK
+
+
+@pytest.mark.parametrize("eps,kw", [(1e-5, {}), (1e-6, {}), (1e-8, {}), (1e-5, {"tc_layout": 1})])
+def test_validate_finds_every_table_in_range(env, eps, kw):
+    """dfmm_validate: device-side bounds check of every index table of the plan
+    (and of the work tiles of the workspaces laid out by an apply) passes on
+    plans of the tensor-core, FP32, FP64 and real-block forms, on an adaptive
+    tree with W and X lists."""
+    torch, dfmm = env
+    p = workloads.clustered(8.0, 3, 6000, n_clusters=3, spread=0.08)
+    g = dfmm.Plan(p, 8.0, eps, leaf_max=16, **kw)
+    f = torch.as_tensor(workloads.densities(p.shape[0], 2, 3), device="cuda").to(g.dtype)
+    g.apply(f)
+    torch.cuda.synchronize()
+    g.validate()
+
+
+def test_validate_reports_an_entry_out_of_range(env):
+    """The planted check (a scratch copy of one pair table with one source row
+    at its bound; the plan is not touched) makes dfmm_validate fail with
+    DFMM_ERR_DEVICE and name the table; the plan still validates and applies."""
+    torch, dfmm = env
+    p = workloads.sphere(4.0, 33)
+    g = dfmm.Plan(p, 4.0, 1e-5)
+    with pytest.raises(dfmm.DfmmError) as e:
+        g.validate(plant=True)
+    assert e.value.code == dfmm.ERR_DEVICE
+    assert "planted" in str(e.value) and "entry 0" in str(e.value)
+    g.validate()
+    f = workloads.densities(p.shape[0], 1, 33)
+    u = g.apply(torch.as_tensor(f.astype(np.complex64), device="cuda")).cpu().numpy()
+    t = np.arange(0, p.shape[0], 50)
+    assert OD.rel_err(u[:, t].astype(np.complex128), OD.direct(p, f, t)) <= 1e-5
