@@ -309,6 +309,15 @@ def run_ours(args, wl):
         elif name in ("p2p", "p2l_eval") and "tflops" in entry:
             entry["frac"] = entry["tflops"] / pk["fp32_tflops"]
             entry["bound"] = ("fp64" if fp64 else "fp32") + " FMA (16 + 8 nrhs flops per interaction)"
+            if name == "p2p" and probes and not fp64:
+                # each interaction issues one reciprocal square root and one sine + cosine
+                # pair on the special-function unit: the measured rates bound the kernel
+                # (once per pass of up to 4 right-hand sides)
+                passes = -(-nrhs // (1 if nrhs == 1 else (2 if nrhs == 2 else 4)))
+                t_mufu = st["p2p_interactions"] * passes * (1.0 / (probes["sincos_gops"] * 1e9) +
+                                                            1.0 / (probes["rsqrt_gops"] * 1e9))
+                entry["mufu_bound_ms"] = 1e3 * t_mufu
+                entry["frac_of_mufu_bound"] = 1e3 * t_mufu / per
         elif "gbs" in entry:
             entry["frac"] = entry["gbs"] / pk["hbm_gbs"]
             entry["bound"] = "hbm"
