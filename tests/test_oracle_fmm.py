@@ -73,12 +73,15 @@ def test_symmetry_mapped_representation_is_accurate():
 
 
 def test_separation_ranks_near_table1():
+    """Table 1's ranks at eps 1e-4, 1e-6 and 1e-8 (at 1e-8 with the 800-row sketch
+    that ranks near 150 need: 2r pivots)."""
     gold = json.load(open(os.path.join(GOLD, "table1_separation_rank.json")))
-    for eps_key in ("1e-4", "1e-6"):
+    for eps_key in ("1e-4", "1e-6", "1e-8"):
         eps = float(eps_key)
+        sketch = 800 if eps < 1e-7 else 400
         for k, w in enumerate((1.0, 2.0, 4.0, 8.0)):
             assert gold["widths"][k] == w
-            r = S.hf_rep(w, 0, max(4.0, w), S.SkelParams(eps_op=eps)).r
+            r = S.hf_rep(w, 0, max(4.0, w), S.SkelParams(eps_op=eps, sketch=sketch)).r
             ref = gold["rank"][eps_key][k]
             assert 0.5 * ref <= r <= 2.0 * ref, (eps, w, r, ref)
 
