@@ -358,7 +358,8 @@ def run_ours(args, wl):
                       "l2": "inputs larger than L2 (plan %.1f GB resident, states re-zeroed each step)" % (st["plan_bytes"] / 1e9),
                       "plan_seconds": plan_s,
                       "plan_phase_seconds": dict(zip(("tree_lists", "skeletons", "rep_upload", "operators", "rows",
-                                                      "near_field", "tc_images"), st["plan_phase_seconds"]))},
+                                                      "near_field", "tc_images", "operators_on_device"),
+                                                     st["plan_phase_seconds"]))},
            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
            "graph_ms_per_step": graph_ms,
            "e2e": {"value": N * nrhs / (e2e_ms / 1e3), "unit": "points*RHS/s",

@@ -202,7 +202,8 @@ typedef struct {
                                      host, from the disk cache when present); 2 = their upload;
                                      3 = translation operators (M2M, M2L, L2L, P2L projections);
                                      4 = per-point rows (L2P, P2M, M2P); 5 = near-field lists and
-                                     close pairs; 6 = tensor-core operator images; 7 = unused */
+                                     close pairs; 6 = tensor-core operator images; 7 = the part of
+                                     phase 3 spent forming operators on the device */
   double skeleton_phase_seconds[4]; /* phase 1 in detail: 0 = disk cache and samples; 1 = sketch pivots
                                        (the whole host build in the host form); 2 = check-point
                                        pivots; 3 = least-squares factors */

@@ -580,10 +580,23 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
       P->rep_ranks.push_back({(int64_t)l, (int64_t)c, (int64_t)rp.r});
     }
   }
-  auto rank_of = [&](int l, int cell) { return P->reps->get(LV[l].w, cell).r; };
-  cublasHandle_t cb;
-  if (cublasCreate(&cb) != CUBLAS_STATUS_SUCCESS) throw Error(DFMM_ERR_CUDA, "cublasCreate failed");
-  struct CbGuard { cublasHandle_t h; ~CbGuard() { cublasDestroy(h); } } cbg{cb};
+  // ranks per (level, cell), looked up once: the flop counts below take two per pair
+  std::vector<std::vector<int>> rank_cache(nl);
+  auto rank_of = [&](int l, int cell) {
+    std::vector<int>& v = rank_cache[l];
+    const size_t i = (size_t)(cell + 1);   // the LF type (cell -1) at 0
+    if (i >= v.size()) v.resize(i + 1, -1);
+    if (v[i] < 0) v[i] = P->reps->get(LV[l].w, cell).r;
+    return v[i];
+  };
+  // operator formation on the device (FP64 kernel blocks and products), timed
+  // apart within phase 3
+  auto timed_form = [&](OpKind kind, const std::vector<OpSpec>& sp, const std::vector<DevRep>& dr, int Rt, int Rs,
+                        void* out, bool fp64) {
+    const double t = now();
+    form_ops(kind, sp, dr, Rt, Rs, out, fp64, ar, s);
+    ph[7] += now() - t;
+  };
   double m2l_flops = 0, other_flops = 0;
   auto center = [&](int l, int64_t b, int d) { return -0.5 * P->W + (LV[l].h_coords[3 * b + d] + 0.5) * LV[l].w; };
   P->zero_shift = upload(std::vector<float4>{make_float4(0, 0, 0, 0)}, ar, s);
@@ -658,7 +671,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
       F.v.M = R; F.v.Kd = R; F.v.nops = (int)specs.size();
       if (!specs.empty()) {
         F.v.ops = ar.alloc<float2>(((size_t)specs.size() * R * R) * P->cw);
-        form_ops(kOpM2L, specs, dreps, R, R, F.v.ops, P->fp64, cb, ar, s);
+        timed_form(kOpM2L, specs, dreps, R, R, F.v.ops, P->fp64);
       }
       F.v.fam = F_M2L_LF;
       F.v.flops_rhs = 8.0 * rp.r * rp.r * V.n;
@@ -682,7 +695,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
       (void)C;
       F.m2m.M = R; F.m2m.Kd = Rc; F.m2m.nops = 8;
       F.m2m.ops = ar.alloc<float2>(((size_t)8 * R * Rc) * P->cw);
-      form_ops(kOpM2M, specs, dreps, R, Rc, F.m2m.ops, P->fp64, cb, ar, s);
+      timed_form(kOpM2M, specs, dreps, R, Rc, F.m2m.ops, P->fp64);
       op.clear(); pr.clear();
       for (int64_t c = 0; c < Lc.n; ++c) {
         op.push_back(octant_of(&Lc.h_coords[3 * c]));
@@ -708,7 +721,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
       }
       F.l2l.M = R; F.l2l.Kd = Rp; F.l2l.nops = 8;
       F.l2l.ops = ar.alloc<float2>(((size_t)8 * R * Rp) * P->cw);
-      form_ops(kOpL2L, specs, dreps, R, Rp, F.l2l.ops, P->fp64, cb, ar, s);
+      timed_form(kOpL2L, specs, dreps, R, Rp, F.l2l.ops, P->fp64);
       op.clear(); pr.clear();
       for (int64_t c = 0; c < LV[l].n; ++c) {
         op.push_back(octant_of(&LV[l].h_coords[3 * c]));
@@ -782,7 +795,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
         H.m2l.M = R; H.m2l.Kd = R; H.m2l.nops = (int)specs.size();
         if (!specs.empty()) {
           H.m2l.ops = ar.alloc<float2>(((size_t)specs.size() * R * R) * P->cw);
-          form_ops(kOpM2L, specs, dreps, R, R, H.m2l.ops, P->fp64, cb, ar, s);
+          timed_form(kOpM2L, specs, dreps, R, R, H.m2l.ops, P->fp64);
         }
         H.m2l.src_rows = (int64_t)H.out_keys.size();
         H.m2l.dst_rows = (int64_t)H.in_keys.size();
@@ -808,7 +821,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
           }
         H.m2m.M = R; H.m2m.Kd = Rc; H.m2m.nops = (int)specs.size();
         H.m2m.ops = ar.alloc<float2>((std::max<size_t>(1, specs.size()) * R * Rc) * P->cw);
-        form_ops(kOpM2M, specs, dreps, R, Rc, H.m2m.ops, P->fp64, cb, ar, s);
+        timed_form(kOpM2M, specs, dreps, R, Rc, H.m2m.ops, P->fp64);
         op.clear(); pr.clear();
         for (size_t k = 0; k < H.out_keys.size(); ++k) {
           int b = H.out_keys[k] / H.nd, d = H.out_keys[k] % H.nd;
@@ -850,7 +863,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
           }
         H.l2l.M = R; H.l2l.Kd = Hp.R; H.l2l.nops = (int)specs.size();
         H.l2l.ops = ar.alloc<float2>((std::max<size_t>(1, specs.size()) * R * Hp.R) * P->cw);
-        form_ops(kOpL2L, specs, dreps, R, Hp.R, H.l2l.ops, P->fp64, cb, ar, s);
+        timed_form(kOpL2L, specs, dreps, R, Hp.R, H.l2l.ops, P->fp64);
         op.clear(); pr.clear();
         for (size_t k = 0; k < Hp.in_keys.size(); ++k) {
           int b = Hp.in_keys[k] / Hp.nd, d = Hp.in_keys[k] % Hp.nd;
@@ -890,7 +903,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
         }
       F.l2l.M = F.R; F.l2l.Kd = Hp.R; F.l2l.nops = (int)specs.size();
       F.l2l.ops = ar.alloc<float2>((std::max<size_t>(1, specs.size()) * F.R * Hp.R) * P->cw);
-      form_ops(kOpL2L, specs, dreps, F.R, Hp.R, F.l2l.ops, P->fp64, cb, ar, s);
+      timed_form(kOpL2L, specs, dreps, F.R, Hp.R, F.l2l.ops, P->fp64);
       std::vector<int32_t> op;
       std::vector<int2> pr;
       for (size_t k = 0; k < Hp.in_keys.size(); ++k) {
@@ -966,8 +979,8 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
       ArenaMark mk(ar);
       double* dlp = ar.alloc<double>(lp.size());
       DFMM_CUDA(cudaMemcpyAsync(dlp, lp.data(), lp.size() * 8, cudaMemcpyHostToDevice, s));
-      form_rows(true, dreps[ridx.at({l, -1})], dlp, row, F.l2p_rows, P->fp64, cb, ar, s);
-      form_p2m_rows(dreps[ridx.at({l, -1})], dlp, row, F.p2m_rows, P->fp64, cb, ar, s);
+      form_rows(true, dreps[ridx.at({l, -1})], dlp, row, F.l2p_rows, P->fp64, ar, s);
+      form_p2m_rows(dreps[ridx.at({l, -1})], dlp, row, F.p2m_rows, P->fp64, ar, s);
     }
     other_flops += 8.0 * F.r * (double)row;
   }
@@ -1000,7 +1013,7 @@ void build_plan(dfmm_plan_s* P, const double* d_points, cudaStream_t s) {
       ArenaMark mk(ar);
       double* dlp = ar.alloc<double>(lp.size());
       DFMM_CUDA(cudaMemcpyAsync(dlp, lp.data(), lp.size() * 8, cudaMemcpyHostToDevice, s));
-      form_rows(false, dreps[ridx.at({la, -1})], dlp, row, g.rows, P->fp64, cb, ar, s);
+      form_rows(false, dreps[ridx.at({la, -1})], dlp, row, g.rows, P->fp64, ar, s);
     }
     P->m2p.push_back(g);
   }

@@ -3,9 +3,10 @@
 // Every operator is a product of bounded factors (an orthonormal projection,
 // the kernel matrix between check and equivalent points, and the inverse
 // triangular factor of the source basis), formed in FP64 and rounded once to
-// complex64 for the apply kernels (kept in complex128 for the FP64 form).  The kernel matrices are evaluated by a
-// hand-written FP64 kernel; the two small products per operator are plain
-// batched ZGEMMs (cuBLAS).
+// complex64 for the apply kernels (kept in complex128 for the FP64 form).  The
+// kernel matrices and the products (a tiled FP64 complex GEMM) are the
+// library's own kernels: the batched ZGEMM of the vendor library spends
+// seconds on its first call in a process.
 #include <cmath>
 
 #include "operators.h"
@@ -14,11 +15,6 @@ namespace dfmm {
 
 namespace {
 
-#define DFMM_CUBLAS(call)                                                             \
-  do {                                                                                \
-    cublasStatus_t st_ = (call);                                                      \
-    if (st_ != CUBLAS_STATUS_SUCCESS) throw Error(-4, std::string(#call) + " failed"); \
-  } while (0)
 
 __device__ __forceinline__ double2 green64(double x0, double x1, double x2, const double* y) {
   double dx = x0 - y[0], dy = x1 - y[1], dz = x2 - y[2];
@@ -85,12 +81,80 @@ void store_out(const double2* in, void* out, int64_t at, int64_t n, bool fp64, c
   }
 }
 
-// row-major C (m x n) = A (m x k) B (k x n), batched through pointer arrays
-void gemm_rm_batched(cublasHandle_t cb, int m, int n, int k, const double2** A, const double2** B, double2** C,
-                     int batch) {
-  const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
-  DFMM_CUBLAS(cublasZgemmBatched(cb, CUBLAS_OP_N, CUBLAS_OP_N, n, m, k, &one, (const cuDoubleComplex**)B, n,
-                                 (const cuDoubleComplex**)A, k, &zero, (cuDoubleComplex**)C, n, batch));
+// Row-major complex128 products C_b = A_b op(B_b) for a batch of pointer
+// triples: A_b is M x K (lda), B_b is K x N (ldb), or N x K with tb (then
+// op(B) = B^T, no conjugation), C_b is M x N (ldc).  One CTA of 256 threads
+// computes a 32 x 32 block of C (4 entries per thread, rows ty + 8 i), with
+// K in steps of 16 through shared memory.
+constexpr int ZT = 32, ZK = 16;
+
+__global__ __launch_bounds__(256) void zgemm_kernel(const double2* const* __restrict__ Ap,
+                                                    const double2* const* __restrict__ Bp, double2* const* __restrict__ Cp,
+                                                    int M, int N, int K, int lda, int ldb, int ldc, bool tb) {
+  __shared__ double2 As[ZT][ZK + 1];
+  __shared__ double2 Bs[ZK][ZT + 1];
+  const double2* A = Ap[blockIdx.z];
+  const double2* B = Bp[blockIdx.z];
+  double2* C = Cp[blockIdx.z];
+  const int tid = threadIdx.x, tx = tid % ZT, ty = tid / ZT;
+  const int row0 = blockIdx.y * ZT, col0 = blockIdx.x * ZT;
+  double2 acc[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) acc[i] = make_double2(0.0, 0.0);
+  for (int k0 = 0; k0 < K; k0 += ZK) {
+    for (int e = tid; e < ZT * ZK; e += 256) {
+      const int r = e / ZK, kk = e % ZK;
+      const int gr = row0 + r, gk = k0 + kk;
+      As[r][kk] = (gr < M && gk < K) ? A[(int64_t)gr * lda + gk] : make_double2(0.0, 0.0);
+    }
+    for (int e = tid; e < ZT * ZK; e += 256) {
+      int kk, c;
+      if (tb) { c = e / ZK; kk = e % ZK; } else { kk = e / ZT; c = e % ZT; }
+      const int gk = k0 + kk, gc = col0 + c;
+      double2 v = make_double2(0.0, 0.0);
+      if (gk < K && gc < N) v = tb ? B[(int64_t)gc * ldb + gk] : B[(int64_t)gk * ldb + gc];
+      Bs[kk][c] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < ZK; ++kk) {
+      const double2 b = Bs[kk][tx];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const double2 a = As[ty + 8 * i][kk];
+        acc[i].x = fma(a.x, b.x, fma(-a.y, b.y, acc[i].x));
+        acc[i].y = fma(a.x, b.y, fma(a.y, b.x, acc[i].y));
+      }
+    }
+    __syncthreads();
+  }
+  const int c = col0 + tx;
+  if (c < N)
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int r = row0 + ty + 8 * i;
+      if (r < M) C[(int64_t)r * ldc + c] = acc[i];
+    }
+}
+
+void zgemm(const double2* const* A, const double2* const* B, double2* const* C, int batch, int M, int N, int K,
+           int lda, int ldb, int ldc, bool tb, cudaStream_t s) {
+  if (batch <= 0 || M <= 0 || N <= 0) return;
+  const dim3 grid((unsigned)((N + ZT - 1) / ZT), (unsigned)((M + ZT - 1) / ZT), (unsigned)batch);
+  if (grid.y > 65535u || grid.z > 65535u) throw Error(-5, "operator formation: product too large for one launch");
+  zgemm_kernel<<<grid, 256, 0, s>>>(A, B, C, M, N, K, lda, ldb, ldc, tb);
+  DFMM_CUDA(cudaGetLastError());
+}
+
+// one product through a device pointer triple held in `ar`
+void zgemm1(const double2* A, const double2* B, double2* C, int M, int N, int K, int lda, int ldb, int ldc, bool tb,
+            DevArena& ar, cudaStream_t s) {
+  const void* h[3] = {A, B, C};
+  const void** d = ar.alloc<const void*>(3);
+  DFMM_CUDA(cudaMemcpyAsync(d, h, sizeof h, cudaMemcpyHostToDevice, s));
+  zgemm((const double2* const*)d, (const double2* const*)(d + 1), (double2* const*)(d + 2), 1, M, N, K, lda, ldb,
+        ldc, tb, s);
+  DFMM_CUDA(cudaStreamSynchronize(s));   // the pointer triple is released with the caller's mark
 }
 
 std::vector<double2> pad_matrix(const std::vector<cd>& M, int rows, int cols, int Rrows, int Rcols,
@@ -144,7 +208,7 @@ DevRep upload_rep(const Rep& rep, int R, DevArena& ar, cudaStream_t s) {
 }
 
 void form_ops(OpKind kind, const std::vector<OpSpec>& ops, const std::vector<DevRep>& reps, int Rt, int Rs,
-              void* out, bool fp64, cublasHandle_t cb, DevArena& ar, cudaStream_t s) {
+              void* out, bool fp64, DevArena& ar, cudaStream_t s) {
   if (ops.empty()) return;
   ArenaMark mark(ar);
   DevRep* d_reps = ar.alloc<DevRep>(reps.size());
@@ -161,7 +225,6 @@ void form_ops(OpKind kind, const std::vector<OpSpec>& ops, const std::vector<Dev
   std::vector<OpDev> h_ops(batch);
   std::vector<const double2*> hA(batch), hB(batch);
   std::vector<double2*> hC(batch);
-  DFMM_CUBLAS(cublasSetStream(cb, s));
   for (size_t start = 0; start < ops.size(); start += batch) {
     int nb = (int)std::min<size_t>(batch, ops.size() - start);
     for (int k = 0; k < nb; ++k) {
@@ -183,7 +246,7 @@ void form_ops(OpKind kind, const std::vector<OpSpec>& ops, const std::vector<Dev
     DFMM_CUDA(cudaMemcpyAsync(pA, hA.data(), nb * sizeof(void*), cudaMemcpyHostToDevice, s));
     DFMM_CUDA(cudaMemcpyAsync(pB, hB.data(), nb * sizeof(void*), cudaMemcpyHostToDevice, s));
     DFMM_CUDA(cudaMemcpyAsync(pC, hC.data(), nb * sizeof(void*), cudaMemcpyHostToDevice, s));
-    gemm_rm_batched(cb, Rt, Rs, 2 * Rt, pA, pB, pC, nb);
+    zgemm(pA, pB, pC, nb, Rt, Rs, 2 * Rt, 2 * Rt, Rs, Rs, false, s);
     // T2 = T1 (Rt x Rs) Rinv_s (Rs x Rs)
     DFMM_CUDA(cudaStreamSynchronize(s));
     for (int k = 0; k < nb; ++k) {
@@ -195,22 +258,20 @@ void form_ops(OpKind kind, const std::vector<OpSpec>& ops, const std::vector<Dev
     DFMM_CUDA(cudaMemcpyAsync(pA, hA.data(), nb * sizeof(void*), cudaMemcpyHostToDevice, s));
     DFMM_CUDA(cudaMemcpyAsync(pB, hB.data(), nb * sizeof(void*), cudaMemcpyHostToDevice, s));
     DFMM_CUDA(cudaMemcpyAsync(pC, hC.data(), nb * sizeof(void*), cudaMemcpyHostToDevice, s));
-    gemm_rm_batched(cb, Rt, Rs, Rs, pA, pB, pC, nb);
+    zgemm(pA, pB, pC, nb, Rt, Rs, Rs, Rs, Rs, Rs, false, s);
     store_out(T2, out, (int64_t)start * Rt * Rs, (int64_t)nb * Rt * Rs, fp64, s);
     DFMM_CUDA(cudaStreamSynchronize(s));
   }
 }
 
 void form_rows(bool incoming, const DevRep& rep, const double* d_pts, int64_t n, void* out, bool fp64,
-               cublasHandle_t cb, DevArena& ar, cudaStream_t s) {
+               DevArena& ar, cudaStream_t s) {
   if (n <= 0) return;
   ArenaMark mark(ar);
   int R = rep.R;
   int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)((512ull << 20) / (2 * R * sizeof(double2)))));
   double2* K = ar.alloc<double2>((size_t)chunk * R);
   double2* T = ar.alloc<double2>((size_t)chunk * R);
-  const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
-  DFMM_CUBLAS(cublasSetStream(cb, s));
   for (int64_t st = 0; st < n; st += chunk) {
     int64_t m = std::min(chunk, n - st);
     int64_t ne = m * R;
@@ -218,23 +279,20 @@ void form_rows(bool incoming, const DevRep& rep, const double* d_pts, int64_t n,
                                                                    incoming ? rep.wa2 : nullptr, rep.r, R, K);
     const double2* Rinv = incoming ? rep.Ri_inv : rep.Ro_inv;
     // row-major T (m x R) = K (m x R) Rinv (R x R)
-    DFMM_CUBLAS(cublasZgemm(cb, CUBLAS_OP_N, CUBLAS_OP_N, R, (int)m, R, &one, (const cuDoubleComplex*)Rinv, R,
-                            (const cuDoubleComplex*)K, R, &zero, (cuDoubleComplex*)T, R));
+    zgemm1(K, Rinv, T, (int)m, R, R, R, R, R, false, ar, s);
     store_out(T, out, st * R, ne, fp64, s);
   }
   DFMM_CUDA(cudaStreamSynchronize(s));
 }
 
-void form_p2m_rows(const DevRep& rep, const double* d_pts, int64_t n, void* out, bool fp64, cublasHandle_t cb,
-                   DevArena& ar, cudaStream_t s) {
+void form_p2m_rows(const DevRep& rep, const double* d_pts, int64_t n, void* out, bool fp64, DevArena& ar,
+                   cudaStream_t s) {
   if (n <= 0) return;
   ArenaMark mark(ar);
   const int R = rep.R, K2 = 2 * R;
   int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(n, (int64_t)((512ull << 20) / (3 * R * sizeof(double2)))));
   double2* K = ar.alloc<double2>((size_t)chunk * K2);
   double2* T = ar.alloc<double2>((size_t)chunk * R);
-  const cuDoubleComplex one = make_cuDoubleComplex(1.0, 0.0), zero = make_cuDoubleComplex(0.0, 0.0);
-  DFMM_CUBLAS(cublasSetStream(cb, s));
   for (int64_t st = 0; st < n; st += chunk) {
     const int64_t m = std::min(chunk, n - st);
     const int64_t ne = m * K2;
@@ -242,8 +300,7 @@ void form_p2m_rows(const DevRep& rep, const double* d_pts, int64_t n, void* out,
     rows_kmat_kernel<<<(unsigned)((ne + 255) / 256), 256, 0, s>>>(d_pts + 3 * st, m, rep.a2, nullptr, 2 * rep.r, K2,
                                                                    K);
     // row-major T (m x R) = K (m x 2R) PoutH^T, PoutH = Qo^H W (R x 2R, row-major)
-    DFMM_CUBLAS(cublasZgemm(cb, CUBLAS_OP_T, CUBLAS_OP_N, R, (int)m, K2, &one, (const cuDoubleComplex*)rep.PoutH,
-                            K2, (const cuDoubleComplex*)K, K2, &zero, (cuDoubleComplex*)T, R));
+    zgemm1(K, rep.PoutH, T, (int)m, R, K2, K2, K2, R, true, ar, s);
     store_out(T, out, st * R, m * R, fp64, s);
   }
   DFMM_CUDA(cudaStreamSynchronize(s));

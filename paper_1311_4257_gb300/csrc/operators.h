@@ -1,7 +1,5 @@
 // Plan-time formation of the translation operators in FP64 (see operators.cu).
 #pragma once
-#include <cublas_v2.h>
-
 #include <vector>
 
 #include "common.h"
@@ -40,7 +38,7 @@ struct OpSpec {
 // them as complex64 [n][R_t][R_s] into out (device), or as complex128 when
 // fp64 is set (the FP64 form of the apply).
 void form_ops(OpKind kind, const std::vector<OpSpec>& ops, const std::vector<DevRep>& reps, int Rt, int Rs,
-              void* out, bool fp64, cublasHandle_t cb, DevArena& ar, cudaStream_t s);
+              void* out, bool fp64, DevArena& ar, cudaStream_t s);
 
 // Rows for evaluating a representation at points:
 //   L2P (incoming): row_i = G(y_i - c, a_in) W Ri^{-1}
@@ -48,13 +46,13 @@ void form_ops(OpKind kind, const std::vector<OpSpec>& ops, const std::vector<Dev
 // pts: device FP64 [n][3] of y_i - c (local), written as complex64 [n][R]
 // (complex128 when fp64 is set).
 void form_rows(bool incoming, const DevRep& rep, const double* d_local_pts, int64_t n, void* out, bool fp64,
-               cublasHandle_t cb, DevArena& ar, cudaStream_t s);
+               DevArena& ar, cudaStream_t s);
 
 // Rows of P2M through the outgoing representation (Eq. 2 with the
 // least-squares projection): row_i = Qo^H W G(a2, y_i - c), the outgoing
 // state a unit source at y_i produces.  pts: device FP64 [n][3] of y_i - c;
 // written as complex64 [n][R] (complex128 when fp64 is set).
-void form_p2m_rows(const DevRep& rep, const double* d_local_pts, int64_t n, void* out, bool fp64, cublasHandle_t cb,
-                   DevArena& ar, cudaStream_t s);
+void form_p2m_rows(const DevRep& rep, const double* d_local_pts, int64_t n, void* out, bool fp64, DevArena& ar,
+                   cudaStream_t s);
 
 }  // namespace dfmm
