@@ -124,3 +124,31 @@ def test_fp64_entry_points_agree(sphere4):
     # the GMRES driver works on complex64 vectors: FP64 plans are refused
     with pytest.raises(DfmmError):
         g.solve(torch.ones(p.shape[0], dtype=torch.complex64, device="cuda"))
+
+
+def test_fp64_captured_and_merged_batch_forms(sphere4):
+    """A captured apply (dfmm_graph_*) and the merged batch (dfmm_batch_*, with a
+    second FP64 plan of another geometry) on complex128 buffers equal the plain
+    applies; the FP64 stages run per plan inside the batch's waves."""
+    import torch
+    from paper_1311_4257_gb300 import Batch, Plan
+    p, g = sphere4
+    f = workloads.densities(p.shape[0], 2, 5)
+    u = _apply(g, f)
+    fd = torch.as_tensor(f, device="cuda")
+    ud = torch.empty_like(fd)
+    gr = g.graph(fd, ud)
+    gr.launch()
+    torch.cuda.synchronize()
+    assert OD.rel_err(ud.cpu().numpy(), u) <= 1e-14
+    gr.close()
+    p2 = workloads.sphere(4.0, 6, n=3000)
+    g2 = Plan(p2, 4.0, 1e-8)
+    f2 = workloads.densities(p2.shape[0], 1, 6)
+    u2 = _apply(g2, f2)
+    b = Batch([g, g2], [fd, torch.as_tensor(f2, device="cuda")])
+    us = b.launch()
+    torch.cuda.synchronize()
+    assert OD.rel_err(us[0].cpu().numpy(), u) <= 1e-14
+    assert OD.rel_err(us[1].cpu().numpy(), u2) <= 1e-14
+    b.close()
