@@ -209,6 +209,8 @@ typedef struct {
                                        pivots; 3 = least-squares factors */
   int64_t skeleton_types;           /* representation types built or loaded (canonical, up to the
                                        cube's symmetries) */
+  int64_t plan_id;                  /* unique within the process (a destroyed plan's handle may be
+                                       reused by a later plan; its id is not) */
 } dfmm_stats;
 
 int dfmm_plan_stats(dfmm_plan_t plan, dfmm_stats* out);

@@ -49,6 +49,7 @@ int fail(int code, const std::string& msg) {
 // plan with holders is not destroyed.
 std::mutex g_plans_mu;
 std::unordered_map<const void*, int64_t> g_plans;
+int64_t g_next_plan_id = 1;   // under g_plans_mu
 
 struct GemmPlan {
   int M = 0, Kd = 0, nops = 0;
@@ -2118,6 +2119,7 @@ int dfmm_plan(const double* points, int64_t N, double K, double eps, const dfmm_
     {
       std::lock_guard<std::mutex> g(g_plans_mu);
       g_plans[P.get()] = 0;
+      P->stats.plan_id = g_next_plan_id++;
     }
     *out = P.release();
     return DFMM_OK;

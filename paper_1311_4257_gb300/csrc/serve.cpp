@@ -121,7 +121,7 @@ struct dfmm_server_s {
   bool stop = false;
   int fail_next = 0;                    // testing aid: status the next group fails with (0 = none)
   std::thread worker;
-  std::map<std::pair<dfmm_plan_t, int>, size_t> ws_bytes;    // workspace bytes per (plan, nrhs)
+  std::map<std::pair<int64_t, int>, size_t> ws_bytes;       // workspace bytes per (plan id, nrhs)
   // statistics
   int64_t n_done = 0, n_failed = 0, n_applies = 0, rhs_done = 0, points_rhs_done = 0;
   int running = 0, max_running = 0;
@@ -129,14 +129,15 @@ struct dfmm_server_s {
   std::vector<double> lat_ms;
 
   size_t footprint(dfmm_plan_t plan, int nrhs) {
-    auto key = std::make_pair(plan, nrhs);
+    dfmm_stats st{};
+    dfmm_plan_stats(plan, &st);
+    // keyed by the plan's id: a destroyed plan's handle may come back for another plan
+    auto key = std::make_pair(st.plan_id, nrhs);
     auto it = ws_bytes.find(key);
     if (it == ws_bytes.end()) {
       const int64_t w = dfmm_apply_workspace_bytes(plan, nrhs);
       it = ws_bytes.emplace(key, (size_t)std::max<int64_t>(w, 0)).first;
     }
-    dfmm_stats st{};
-    dfmm_plan_stats(plan, &st);
     return 2 * align256((size_t)st.N * nrhs * elem_bytes(st)) + align256(it->second) + 256;
   }
 

@@ -50,7 +50,7 @@ class Stats(ctypes.Structure):
                 ("other_translation_flops", ctypes.c_double), ("hf_ops", ctypes.c_int64 * 32),
                 ("p2p_close_pairs", ctypes.c_int64), ("arith", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("plan_phase_seconds", ctypes.c_double * 8), ("skeleton_phase_seconds", ctypes.c_double * 4),
-                ("skeleton_types", ctypes.c_int64)]
+                ("skeleton_types", ctypes.c_int64), ("plan_id", ctypes.c_int64)]
 
     def to_dict(self) -> dict:
         n = self.n_levels
