@@ -92,11 +92,12 @@ typedef struct {
                               ranks padded to 16) wherever the target rank is at most 128, the
                               real-block form elsewhere; 1 = the real-block form [[Tr, -Ti],
                               [Ti, Tr]] everywhere (ranks padded to 8). */
-  int32_t tc_accumulate;   /* [0] split-complex form: 0 = the hi*hi terms and the cross terms in
-                              separate tensor-memory accumulators (one tile at a time); 1 = one
-                              accumulator per component, two tensor-memory buffers, so that a
-                              tile's MMAs overlap the previous tile's epilogue (faster; the cross
-                              terms then take the large terms' accumulation truncation). */
+  int32_t tc_accumulate;   /* [0] split-complex form: 0 = automatic (1 if eps >= 1e-5, else 2);
+                              1 = one tensor-memory accumulator per component, two buffers, so
+                              that a tile's MMAs overlap the previous tile's epilogue (faster;
+                              the cross terms take the large terms' accumulation truncation:
+                              about 1e-6 more error against the FP32 form); 2 = the hi*hi terms
+                              and the cross terms in separate accumulators (one tile at a time). */
   int32_t tc_precision;    /* [0] element type of the scaled hi / lo split of the tensor-core form:
                               0 = FP16 (11 + 11 significant bits, kind::f16); 1 = BF16 (8 + 8 bits,
                               "3xBF16"); 2 = TF32 (11 + 11 bits with an 8-bit exponent, kind::tf32

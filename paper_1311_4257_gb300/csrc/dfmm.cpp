@@ -2067,7 +2067,11 @@ int dfmm_plan(const double* points, int64_t N, double K, double eps, const dfmm_
     if (o.tile_order < 0 || o.tile_order > 2) return fail(DFMM_ERR_INVALID, "tile_order must be 0, 1 or 2");
     if (o.p2p_mode < 0 || o.p2p_mode > 2) return fail(DFMM_ERR_INVALID, "p2p_mode must be 0, 1 or 2");
     if (o.tc_layout < 0 || o.tc_layout > 1) return fail(DFMM_ERR_INVALID, "tc_layout must be 0 or 1");
-    if (o.tc_accumulate < 0 || o.tc_accumulate > 1) return fail(DFMM_ERR_INVALID, "tc_accumulate must be 0 or 1");
+    if (o.tc_accumulate < 0 || o.tc_accumulate > 2) return fail(DFMM_ERR_INVALID, "tc_accumulate must be 0, 1 or 2");
+    // automatic accumulation: one accumulator per component (the MMAs of a tile
+    // overlap the previous tile's epilogue) within the tensor-core form's own
+    // range (eps >= 1e-5); the separate cross-term accumulators below it
+    if (o.tc_accumulate == 0) o.tc_accumulate = eps >= 1e-5 ? 1 : 2;
     if (o.tc_precision < 0 || o.tc_precision > 2) return fail(DFMM_ERR_INVALID, "tc_precision must be 0, 1 or 2");
     if (o.tc_precision != 0 && o.tc_layout == 1)
       return fail(DFMM_ERR_INVALID, "the BF16 and TF32 splits need the split-complex form (tc_layout 0)");

@@ -297,15 +297,16 @@ def test_split_complex_form_matches_real_block_form(nrhs):
     as four real products, the default for ranks up to 128) against the
     real-block form [[Tr, -Ti], [Ti, Tr]] (tc_layout 1), the FP32 CUDA-core form
     and the direct sum of Eq. 1; and its one-accumulator, double-buffered
-    variant (tc_accumulate 1)."""
+    variant (tc_accumulate 1, the automatic choice at eps 1e-5) against the
+    separate-accumulator one (tc_accumulate 2)."""
     p = workloads.sphere(8.0, 0)
     f = workloads.densities(p.shape[0], nrhs, 13)
     u_fp = _apply(_plan(p, 8.0, 1e-5, m2l_mode=1), f)
-    g_cx = _plan(p, 8.0, 1e-5, m2l_mode=2)
+    g_cx = _plan(p, 8.0, 1e-5, m2l_mode=2, tc_accumulate=2)
     assert all(r % 16 == 0 for r in g_cx.stats()["rank"])
     u_cx = _apply(g_cx, f)
     u_rb = _apply(_plan(p, 8.0, 1e-5, m2l_mode=2, tc_layout=1), f)
-    u_one = _apply(_plan(p, 8.0, 1e-5, m2l_mode=2, tc_accumulate=1), f)
+    u_one = _apply(_plan(p, 8.0, 1e-5, m2l_mode=2), f)
     assert OD.rel_err(u_cx, u_fp) < 2e-6
     assert OD.rel_err(u_rb, u_fp) < 2e-6
     assert OD.rel_err(u_one, u_fp) < 4e-6
@@ -324,8 +325,8 @@ def test_bf16_and_tf32_splits():
     p = workloads.sphere(8.0, 0)
     f = workloads.densities(p.shape[0], 1, 17)
     u_fp = _apply(_plan(p, 8.0, 1e-5, m2l_mode=1), f)
-    u_tf = _apply(_plan(p, 8.0, 1e-5, m2l_mode=2, tc_precision=2), f)
-    u_bf = _apply(_plan(p, 8.0, 1e-5, m2l_mode=2, tc_precision=1), f)
+    u_tf = _apply(_plan(p, 8.0, 1e-5, m2l_mode=2, tc_precision=2, tc_accumulate=2), f)
+    u_bf = _apply(_plan(p, 8.0, 1e-5, m2l_mode=2, tc_precision=1, tc_accumulate=2), f)
     e_tf, e_bf = OD.rel_err(u_tf, u_fp), OD.rel_err(u_bf, u_fp)
     assert 0 < e_tf < 2e-6
     assert e_tf < e_bf < 2e-4          # 2^-16 per product, far above the 22-bit splits
