@@ -67,11 +67,17 @@ def build(verbose: bool = False) -> str:
                 errs.append(cmd[2])
     if errs:
         raise RuntimeError("nvcc failed for: " + ", ".join(errs))
-    if cmds or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
+    # the objects of the last link (the bounds-checking build links other objects)
+    stamp = os.path.join(BUILD, "libdfmm.objs")
+    linked = open(stamp).read() if os.path.exists(stamp) else ""
+    if cmds or not os.path.exists(LIB) or linked != "\n".join(objs) or \
+            any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
         link = [nvcc(), "-shared", "-o", LIB] + objs + ARCH + ["-lcublas", "-lcudart"]
         res = subprocess.run(link, capture_output=True, text=True)
         if res.returncode != 0:
             raise RuntimeError("link failed:\n" + res.stdout + res.stderr)
+        with open(stamp, "w") as fh:
+            fh.write("\n".join(objs))
     return LIB
 
 
