@@ -1653,7 +1653,9 @@ void build_images(dfmm_plan_s* P, cudaStream_t s) {
 }
 
 // Bounds checks of every index table of the plan and of the work tiles of
-// every workspace laid out so far (dfmm_validate); names[k] names check k.
+// every workspace laid out so far (dfmm_validate); names[k] names check k.  The
+// caller holds P->ws_mu until the checks have run (a workspace replaced
+// meanwhile would free its tile tables).
 void plan_checks(dfmm_plan_s* P, std::vector<RangeCheck>& c, std::vector<std::string>& names) {
   const int64_t N = P->N;
   auto fields = [&](const std::string& nm, const void* p, int64_t n, int stride, int a, int64_t hi_a, int b = -1,
@@ -1680,7 +1682,6 @@ void plan_checks(dfmm_plan_s* P, std::vector<RangeCheck>& c, std::vector<std::st
     names.push_back(nm);
   };
   fields("permutation", P->perm, N, 1, 0, N);
-  std::lock_guard<std::mutex> g(P->ws_mu);
   int si = 0;
   for (const GemmPlan* gp : all_gemms(P)) {
     const std::string tag = std::string(kFamName[gp->fam]) + " stage " + std::to_string(si++);
@@ -1737,6 +1738,7 @@ void plan_checks(dfmm_plan_s* P, std::vector<RangeCheck>& c, std::vector<std::st
 // non-empty pair table with the source row of its first pair set to its bound.
 // Throws DFMM_ERR_DEVICE naming the first table with an entry out of range.
 void validate_plan(dfmm_plan_s* P, cudaStream_t s, bool plant) {
+  std::lock_guard<std::mutex> g(P->ws_mu);
   std::vector<RangeCheck> c;
   std::vector<std::string> names;
   plan_checks(P, c, names);
