@@ -18,11 +18,14 @@
 //    FP16 (kind::f16, the default), BF16 (kind::f16 with BF16 operands:
 //    "3xBF16", about 16 bits) or TF32 (kind::tf32: "3xTF32", about 22 bits,
 //    half the FP16 rate).  Every tile is 64 bytes per row and K step 32
-//    bytes whatever the type, so one layout serves all three.  hi hi
-//    products go to the accumulators
-//    Re Y, Im Y and the cross terms hi lo + lo hi to a second pair re y, im y
-//    (tensor-core accumulation truncates), added in FP32 by the epilogue.
-//    4 accumulators x r_t <= 512 tensor-memory columns.  12 MMAs per K step.
+//    bytes whatever the type, so one layout serves all three.  12 MMAs per K
+//    step.  The hi hi products go to the accumulators Re Y, Im Y, and the
+//    cross terms hi lo + lo hi either to a second pair re y, im y, added in
+//    FP32 by the epilogue (ONE = false: tensor-core accumulation truncates, so
+//    the small terms keep their own accumulators; 4 r_t <= 512 tensor-memory
+//    columns, one tile at a time), or into Re Y, Im Y as well (ONE = true, the
+//    automatic choice at eps >= 1e-5: 2 r_t columns per buffer and two
+//    buffers, so that a tile's MMAs overlap the previous tile's epilogue).
 //  * Stage = one K chunk of 32: the gathered xr hi, xr lo, xi hi, xi lo tiles
 //    (128 rows x 64 bytes each, 16-byte cp.async) and the operator's Tr hi,
 //    Tr lo, Ti hi, Ti lo tiles (one bulk copy of its plan-time image); 3
