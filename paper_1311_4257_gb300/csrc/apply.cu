@@ -7,14 +7,16 @@
 //    source states (pairs x right-hand sides), and scatter-adds the result
 //    into the target states with vector atomics (targets of one operator are
 //    distinct, different operators meet in L2).  This is the plain CUDA-core
-//    form; the tensor-core form is in m2l_tc.cu.
+//    form; the tensor-core forms are in m2l_cx.cu and m2l_tc.cu.
 //  * p2c_kernel: potentials at check points from points (P2L, X lists), with
 //    the phase 2 pi |x - y| reduced in a compensated form so that far check
 //    points keep full FP32 accuracy.
 //  * p2m_rows_kernel: P2M as a sum of FP64-formed per-point rows.
 //  * l2p_kernel: L2P through precomputed per-point rows (flat row stream).
 //  * rows_kernel: M2P (W lists) through precomputed rows.
-//  * p2p_kernel: the near field (U lists) in FP32 on box-local coordinates.
+//  * p2p_fast_kernel: the near field (U lists) on FP32 coordinates, with the
+//    exact plan-time corrections of the close pairs (p2p_close_kernel,
+//    p2p_close_apply_kernel); p2p_kernel: the same on double-float coordinates.
 #include "apply.h"
 
 #include <type_traits>

@@ -3,11 +3,15 @@
 //
 // Plan: Morton keys, radix sort, octree and list enumeration run on the
 // device (sort.cu, tree.cu); the host groups the lists into per-operator work
-// tables, builds the representations (skeleton.cpp) and the device forms the
-// operators in FP64 (operators.cu).
-// Apply (one stream, no host synchronisation): permute in, P2M, LF-M2M,
-// HF-M2M, HF-L2L + HF-M2L per level, HF->LF L2L, LF-M2L (V), P2L (X), LF-L2L,
-// L2P, M2P (W), P2P (U), permute out.
+// tables and draws the skeleton samples, the device selects the skeletons
+// (skeleton_gpu.cu; host threads with options.skeleton_host) and forms the
+// operators and evaluation rows in FP64 (operators.cu).
+// Apply (one stream, no host synchronisation): permute in, P2M, LF-M2M, the
+// top V list, then per HF level HF-M2M and HF-M2L, HF-L2L, HF->LF L2L, LF-L2L
+// and LF-M2L (V), P2L (X), L2P, M2P (W), P2P (U), permute out.  The tensor-core
+// (m2l_cx.cu, m2l_tc.cu), FP32 (apply.cu) and FP64 (apply64.cu) kernels serve
+// the three arithmetic forms.  Also here: the allocation-free and captured
+// applies, the batched forms, dfmm_validate and the live-plan registry.
 #include "dfmm.h"
 
 #include <algorithm>
