@@ -221,7 +221,11 @@ __global__ __launch_bounds__(QR_T, 1) void pqr_coop_kernel(const QrTask* __restr
   grid.sync();
 
   for (int k = 0; k < kmax_all; ++k) {
-    const bool active = k < kmax && s_state == 0;
+    // every thread reads the task's state before thread 0 may change it below, so
+    // that all threads of the CTA take the same branches (and barriers)
+    const int state0 = s_state;
+    __syncthreads();
+    const bool active = k < kmax && state0 == 0;
     if (active) {
       if (tid == 0) {
         double best = t.cand_s[0];
@@ -233,8 +237,8 @@ __global__ __launch_bounds__(QR_T, 1) void pqr_coop_kernel(const QrTask* __restr
         s_jb = jb;
         if (best <= t.tol * s_r00 || best == 0.0 || jb >= n) s_state = 1;
       }
-      __syncthreads();
     }
+    __syncthreads();
     const bool go = active && s_state == 0;
     if (go) {
       const int jb = s_jb;
