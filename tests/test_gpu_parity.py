@@ -266,6 +266,27 @@ def test_sphere_k16_tensor_cores_against_oracle_fmm(eps, tile_order):
     assert OD.rel_err(u[:, t], OD.direct(p, f, t)) <= max(eps, 5e-6)
 
 
+@pytest.mark.slow
+def test_sphere_k32_against_oracle_fmm():
+    """Sphere diameter 32, N = 321,699 (seed 1), eps 1e-5, the default forms (tensor
+    cores with one accumulator per component, GPU skeleton selection, FP32 near
+    field), against the oracle FMM element by element on all targets (1e-5
+    relative 2-norm) and the direct sum of Eq. 1 on sampled targets: three HF
+    levels (w = 4, 2, 1; about 1M pairs), four times the K = 16 case."""
+    p = workloads.sphere(32.0, 1)
+    assert p.shape[0] == 321699
+    f = workloads.densities(p.shape[0], 1, 32)
+    g = _plan(p, 32.0, 1e-5)
+    st = g.stats()
+    l4 = st["level_w1"] - 2                      # the level of width 4
+    assert st["level_hf_top"] == l4 and st["hf_pairs"][l4] > 0
+    u = _apply(g, f)
+    uo = OF.fmm(OF.Plan(p, 32.0, OF.FMMParams(eps=1e-5)), f)
+    assert OD.rel_err(u, uo) <= 1e-5
+    t = np.random.default_rng(1032).choice(p.shape[0], 300, replace=False)
+    assert OD.rel_err(u[:, t], OD.direct(p, f, t, chunk=8)) <= 1e-5
+
+
 def test_fp32_near_field_matches_double_float_form():
     """The FP32 near field (p2p_mode 2, automatic at eps >= 1e-5) with its exact
     close-pair corrections against the double-float form (p2p_mode 1) and the
