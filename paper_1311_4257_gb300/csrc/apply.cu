@@ -331,8 +331,11 @@ __global__ __launch_bounds__(256) void l2p_kernel(L2PArgs a) {
 // P2M through rows: one warp per leaf, lane l owns the state entries
 // 2 (l + 32 t), 2 (l + 32 t) + 1 (float4 loads); the leaf's point rows are read
 // 4 at a time (4 KB in flight per warp) and weighted by the points' densities
-// (one broadcast load per point and right-hand side).
-template <int Q>
+// (one broadcast load per point and right-hand side).  KB right-hand sides are
+// accumulated per pass over the rows: 1 for a single right-hand side, whose
+// accumulators then take a quarter of the registers, so that more warps
+// (more rows in flight) fit on an SM.
+template <int Q, int KB>
 __global__ __launch_bounds__(256) void p2m_rows_kernel(P2MRowsArgs a) {
   const int64_t jw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
@@ -341,11 +344,11 @@ __global__ __launch_bounds__(256) void p2m_rows_kernel(P2MRowsArgs a) {
   const int R2 = a.R / 2;
   const float4* rows = (const float4*)a.rows;
   float4* st = (float4*)a.state;
-  for (int k0 = 0; k0 < a.nrhs; k0 += 4) {
-    const int nk = min(4, a.nrhs - k0);
-    float4 acc[4][Q];
+  for (int k0 = 0; k0 < a.nrhs; k0 += KB) {
+    const int nk = min(KB, a.nrhs - k0);
+    float4 acc[KB][Q];
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk)
+    for (int kk = 0; kk < KB; ++kk)
 #pragma unroll
       for (int t = 0; t < Q; ++t) acc[kk][t] = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int i = 0; i < job.y; i += 4) {
@@ -362,7 +365,7 @@ __global__ __launch_bounds__(256) void p2m_rows_kernel(P2MRowsArgs a) {
       for (int j = 0; j < 4; ++j) {
         if (i + j >= job.y) break;
 #pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
+        for (int kk = 0; kk < KB; ++kk) {
           if (kk >= nk) break;
           const float2 f = __ldg(a.fs + (int64_t)(job.x + i + j) * a.nrhs + k0 + kk);
 #pragma unroll
@@ -378,7 +381,7 @@ __global__ __launch_bounds__(256) void p2m_rows_kernel(P2MRowsArgs a) {
       }
     }
 #pragma unroll
-    for (int kk = 0; kk < 4; ++kk) {
+    for (int kk = 0; kk < KB; ++kk) {
       if (kk >= nk) break;
 #pragma unroll
       for (int t = 0; t < Q; ++t) {
@@ -780,8 +783,13 @@ void launch_p2m_rows(const P2MRowsArgs& a, cudaStream_t s) {
   if (a.njobs == 0) return;
   if (a.R > 256 || a.R % 2) throw Error(-5, "representation rank must be even and at most 256");
   const unsigned grid = (unsigned)((a.njobs + 7) / 8);
-  if (a.R <= 128) p2m_rows_kernel<2><<<grid, 256, 0, s>>>(a);
-  else p2m_rows_kernel<4><<<grid, 256, 0, s>>>(a);
+  if (a.nrhs == 1) {
+    if (a.R <= 128) p2m_rows_kernel<2, 1><<<grid, 256, 0, s>>>(a);
+    else p2m_rows_kernel<4, 1><<<grid, 256, 0, s>>>(a);
+  } else {
+    if (a.R <= 128) p2m_rows_kernel<2, 4><<<grid, 256, 0, s>>>(a);
+    else p2m_rows_kernel<4, 4><<<grid, 256, 0, s>>>(a);
+  }
   DFMM_CUDA(cudaGetLastError());
 }
 
