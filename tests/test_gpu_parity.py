@@ -193,6 +193,29 @@ def test_sphere_k64_sampled_targets():
     assert OD.rel_err(u[:, t], ud) <= 1e-5
 
 
+def _golden_k64():
+    import os
+    a = np.loadtxt(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "sphere_k64_oracle.txt"))
+    return a[:, 0].astype(np.int64), a[:, 1] + 1j * a[:, 2], a[:, 3] + 1j * a[:, 4]
+
+
+def test_sphere_k64_against_oracle_fmm():
+    """The benchmarked workload (sphere diameter 64, N = 1,286,796, eps 1e-5, the
+    default forms) against the oracle FMM element by element at 1000 sampled
+    targets (1e-5 relative 2-norm) and against the direct sum of Eq. 1 there
+    (eps).  The oracle's values are stored by
+    tests/golden/make_sphere_k64_oracle.py, which calls only the oracle (its FMM
+    takes minutes at this size)."""
+    t, u_or, u_dir = _golden_k64()
+    p = workloads.sphere(64.0, 1)
+    f = workloads.densities(p.shape[0], 1, 64)
+    u = _apply(_plan(p, 64.0, 1e-5), f)[0, t]
+    e_or, e_dir = OD.rel_err(u, u_or), OD.rel_err(u, u_dir)
+    print(f"K 64, 1000 targets: vs oracle FMM {e_or:.2e}, vs direct sum {e_dir:.2e}")
+    assert e_or <= 1e-5
+    assert e_dir <= 1e-5
+
+
 def test_ellipsoid_k128_sampled_targets():
     """Ellipsoid with semi-axes (64, 32, 16), K = 128, N = 1,625,002 (seed 2),
     eps 1e-5, tensor-core form: 200 sampled targets against the direct sum of
