@@ -1,6 +1,7 @@
 """Pins of the oracle's Morton order, octree, directions and lists (Sec. 2.2)
 to hand-computed keys, brute force and the paper's invariants (Prop. 1,
-hierarchical wedges of Fig. 2, exact coverage of all pairs by Alg. 1)."""
+hierarchical wedges of Fig. 2, exact coverage of all pairs by Alg. 1, the
+per-level counts behind the complexity bounds of Sec. 3.4-3.5)."""
 import math
 
 import numpy as np
@@ -222,3 +223,30 @@ def test_active_directions_closed_under_hierarchy():
                     ok = k < P.nchild[pb]
                     used |= set(((P.child_first[pb[ok]] + k) * nd + cd[ok]).tolist())
             assert set(act[l][side].tolist()) == used
+
+
+def test_hf_work_per_level_scales_as_a_surface():
+    """The counting behind the complexity bounds of Sec. 3.4-3.5 (Prop. 2 and 4),
+    for points sampled from a surface with N = O(K^2): a level of width w has
+    O(K^2 / w^2) non-empty boxes, each target (box, direction) O(1) interaction
+    partners, so each HF level O(K^2) M2L pairs.  On spheres of diameter 16 and
+    32 (same sampling density): boxes x w^2 / K^2 stays between 3 and 6, the
+    w = 1 pair count grows with K^2, and the mean number of pairs per target
+    state stays put as K doubles."""
+    stats = {}
+    for K in (16.0, 32.0):
+        T = ot.build_tree(workloads.sphere(K, 1), K, 64)
+        for q in ot.hf_lists(T):
+            if q.tgt.size == 0:
+                continue
+            nd = ot.n_directions(q.w)
+            states = np.unique(q.tgt * nd + q.dir_in).size
+            stats[(K, q.w)] = (T.levels[q.l].n, q.tgt.size, q.tgt.size / states)
+    for (K, w), (boxes, pairs, per_state) in stats.items():
+        if w <= 2:
+            assert 3.0 <= boxes * w * w / (K * K) <= 6.0, (K, w, boxes)
+            assert per_state <= 40.0, (K, w, per_state)
+    ratio = stats[(32.0, 1.0)][1] / stats[(16.0, 1.0)][1]
+    assert 3.5 <= ratio <= 4.5, ratio                       # O(K^2) pairs at a level
+    a, b = stats[(16.0, 1.0)][2], stats[(32.0, 1.0)][2]
+    assert abs(a - b) <= 0.2 * max(a, b), (a, b)            # O(1) per target state
