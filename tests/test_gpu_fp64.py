@@ -78,7 +78,7 @@ def test_sphere_k4_eps1e8_against_direct_and_oracle(sphere4):
           f"{OD.rel_err(uo, ud):.3e}")
     assert e_dir <= 1e-8, e_dir
     # same skeletons and operators, FP64 on both sides: only the rounding order
-    # differs (cuBLAS vs numpy products, atomics), amplified by the inverse
+    # differs (the library's FP64 GEMMs vs numpy products, atomics), amplified by the inverse
     # factors R^-1 whose condition reaches 1 / eps_op; measured 1.2e-10
     assert e_fmm <= 1e-9, e_fmm
 
